@@ -1,0 +1,160 @@
+/*
+ * gbsp.h -- C ABI of the GB300 (sm_103a) sparse-matrix library: CSR SpMM and SDDMM.
+ *
+ * The two operations are the paper's problem statements (Section II-A):
+ *   SpMM  (Eq. 1):  C = A B,  A sparse M x K in CSR, B dense K x N, C dense M x N.
+ *   SDDMM (Eq. 2):  out = S o (X Y^T) sampled on the pattern of S, i.e. for every stored
+ *                   entry p = (i, j) of S:  out[p] = S_ij * <X_i, Y_j>,
+ *                   with X dense M x Kd and Y dense N x Kd.
+ * The paper writes SpMM as Y = A X with A K x N and X N x D, and SDDMM as
+ * Y = A o (B C) with B N x D and C D x N; here the sparse operand is A (or S), the dense
+ * feature width is N (SpMM) or Kd (SDDMM), and Y is stored row-major as the transpose of
+ * the paper's C so that every gathered row is contiguous.
+ *
+ * Conventions for every entry point
+ *   - All array arguments are DEVICE pointers unless a parameter says "host".  The caller
+ *     owns all memory; the library never frees caller memory.
+ *   - Dense operands are row-major with a leading dimension ld >= cols (in elements).
+ *   - CSR: rowptr is int32[rows + 1] with rowptr[0] = 0 and rowptr[rows] = nnz; colidx is
+ *     int32[nnz].  Column indices need not be sorted; repeated indices are summed by SpMM
+ *     and computed entry by entry by SDDMM.  rows, cols, N, Kd and nnz must be < 2^31.
+ *   - SpMM overwrites C (no accumulation).  SDDMM writes out[] in the CSR order of S.
+ *   - Calls are asynchronous on the given stream (a cudaStream_t passed as void*; NULL is
+ *     the legacy default stream).  Argument errors are returned synchronously and launch
+ *     nothing; a failed launch returns GBSP_ERR_CUDA.  Kernel faults surface at the next
+ *     synchronisation, as for any CUDA call.
+ *   - Inputs are not checked for CSR validity unless opts->validate is set (which costs a
+ *     synchronisation); gbsp_csr_validate is the standalone check.  Out-of-range column
+ *     indices in an unchecked call are undefined behaviour.
+ *   - Results are deterministic: no floating-point atomics; a given variant, launch shape
+ *     and input always produce the same bits.
+ *   - The entry points are thread-safe; the last-error message is per host thread.
+ */
+#ifndef GBSP_H
+#define GBSP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GBSP_OK = 0,
+    GBSP_ERR_INVALID_ARG = -1, /* null pointer, negative size, ld < cols, dtype mismatch */
+    GBSP_ERR_INVALID_CSR = -2, /* validation found a malformed CSR */
+    GBSP_ERR_ALIGN = -3,       /* a vectorised variant was forced on unaligned operands */
+    GBSP_ERR_UNSUPPORTED = -4, /* a combination this build does not implement */
+    GBSP_ERR_CUDA = -5,        /* a CUDA runtime call or launch failed */
+    GBSP_ERR_OOM = -6,         /* library workspace could not be allocated */
+    GBSP_ERR_TIMEOUT = -7      /* a bounded device-side wait gave up */
+} gbsp_status;
+
+typedef enum {
+    GBSP_F32 = 0,  /* IEEE binary32 */
+    GBSP_BF16 = 1, /* bfloat16, stored as uint16 bits */
+    GBSP_E4M3 = 2  /* FP8 E4M3 (OCP), stored as uint8 codes, with one FP32 scale per row */
+} gbsp_dtype;
+
+/* Kernel variants of SpMM / SDDMM.  AUTO lets the library choose. */
+typedef enum {
+    GBSP_VARIANT_AUTO = 0,
+    GBSP_VARIANT_ROWSPLIT = 1, /* one warp per row, vectorised gathers */
+    GBSP_VARIANT_MERGE = 2,    /* nnz-balanced merge-path split with a carry fix-up pass */
+    GBSP_VARIANT_SCALAR = 3    /* unvectorised, any width / alignment */
+} gbsp_variant;
+
+/* A sparse matrix in CSR form (all pointers device). */
+typedef struct {
+    int64_t rows, cols, nnz;
+    const int32_t *rowptr;   /* int32[rows + 1] */
+    const int32_t *colidx;   /* int32[nnz] */
+    const void *vals;        /* nnz values of type dtype */
+    const float *row_scale;  /* E4M3 only: float[rows], value = row_scale[i] * code; else NULL */
+    int32_t dtype;           /* gbsp_dtype */
+} gbsp_csr;
+
+/* A dense row-major matrix (data device). */
+typedef struct {
+    void *data;
+    int64_t rows, cols, ld;  /* ld in elements, >= cols */
+    const float *row_scale;  /* E4M3 only: float[rows]; else NULL */
+    int32_t dtype;           /* gbsp_dtype */
+} gbsp_dense;
+
+/* Per-call options; a NULL pointer means all defaults (zero-initialised struct). */
+typedef struct {
+    int32_t variant;   /* gbsp_variant */
+    int32_t validate;  /* nonzero: run gbsp_csr_validate first (synchronises the stream) */
+    int32_t unroll;    /* 0 = default; else gathers in flight per lane (1, 2, 4 or 8) */
+    int32_t ctas_per_sm; /* merge-path grid: CTAs per SM (0 = default) */
+} gbsp_opts;
+
+/* ---- plain FP32 forms (spec signatures), legacy default stream --------------- */
+
+/* SpMM, Eq. 1: C[i, :] = sum over p in row i of vals[p] * B[colidx[p], :].
+ * rowptr int32[M+1], colidx int32[nnz], vals float[nnz], B float[K x N] (ld = N),
+ * C float[M x N] (ld = N, overwritten).  Returns a gbsp_status. */
+int spmm_csr(const int32_t *rowptr, const int32_t *colidx, const float *vals, const float *B,
+             float *C, int64_t M, int64_t K, int64_t N);
+
+/* SDDMM, Eq. 2: out[p] = svals[p] * <X[i, :], Y[colidx[p], :]> for every p in row i.
+ * rowptr int32[M+1], colidx int32[nnz], svals float[nnz], X float[M x Kd] (ld = Kd),
+ * Y float[N x Kd] (ld = Kd), out float[nnz] (overwritten).  Returns a gbsp_status. */
+int sddmm_csr(const int32_t *rowptr, const int32_t *colidx, const float *svals, const float *X,
+              const float *Y, float *out, int64_t M, int64_t N, int64_t Kd);
+
+/* ---- general forms ----------------------------------------------------------------- */
+
+/* SpMM (Eq. 1) with dtype, leading dimensions, variant and stream.
+ * Supported dtype pairs (A, B) -> C: (F32, F32) -> F32, (BF16, BF16) -> F32 and
+ * (E4M3, E4M3) -> F32 with per-row scales on both A (s_i) and B (t_k):
+ *   C[i, n] = s_i * sum_p qa_p * t_{colidx[p]} * qb[colidx[p], n].
+ * Accumulation is FP32 in every form.  B->rows must equal A->cols, C is A->rows x B->cols. */
+int spmm_csr_ex(const gbsp_csr *A, const gbsp_dense *B, gbsp_dense *C, const gbsp_opts *opts,
+                void *stream);
+
+/* SDDMM (Eq. 2) with dtype, leading dimensions and stream.
+ * Supported (S, X, Y): all F32; S F32 with X, Y BF16; S F32 with X, Y E4M3 (per-row
+ * scales u_i on X and v_j on Y: out[p] = s_p * u_i * v_j * <qx_i, qy_j>).
+ * out is float[S->nnz] in CSR order.  X->rows = S->rows, Y->rows = S->cols,
+ * X->cols = Y->cols = Kd. */
+int sddmm_csr_ex(const gbsp_csr *S, const gbsp_dense *X, const gbsp_dense *Y, float *out,
+                 const gbsp_opts *opts, void *stream);
+
+/* Checks a CSR on the device: rowptr[0] = 0, rowptr non-decreasing, rowptr[rows] = nnz,
+ * 0 <= colidx < cols.  Writes the number of violations to *n_bad (host pointer) and
+ * returns GBSP_OK if it is zero, GBSP_ERR_INVALID_CSR otherwise.  Synchronises stream. */
+int gbsp_csr_validate(const gbsp_csr *A, void *stream, int64_t *n_bad);
+
+/* ---- precision conversion (the roundings of the BF16 / E4M3 forms) -------------------- */
+
+/* out[i] = bfloat16 round-to-nearest-even of x[i]; n elements (x float, out uint16). */
+int gbsp_quantize_bf16(const float *x, uint16_t *out, int64_t n, void *stream);
+
+/* Per-row scaled E4M3: for each row r, scale[r] = max|x| / 448 in FP32 (1 for an all-zero
+ * or empty row) and q = E4M3 round-to-nearest-even, saturating, of x / scale[r] (FP32
+ * division).  Rows are CSR segments when rowptr (device, int32[nrows+1]) is non-NULL,
+ * otherwise nrows dense rows of ncols entries with leading dimension ld (q uses ld too). */
+int gbsp_quantize_e4m3_rows(const float *x, const int32_t *rowptr, int64_t nrows, int64_t ncols,
+                            int64_t ld, uint8_t *q, float *scale, void *stream);
+
+/* ---- errors ------------------------------------------------------------------------ */
+
+const char *gbsp_status_string(int status);
+/* Status and message of the last failing call on this host thread (GBSP_OK if none). */
+int gbsp_get_last_error(void);
+const char *gbsp_last_error_message(void);
+
+/* Number of SMs of the current device as the library sees it (0 on error). */
+int gbsp_device_sm_count(void);
+
+/* Number of CUDA kernels this library has launched in the process so far (all threads).
+ * Benchmarks difference it around a timed region to count the library's launches. */
+int64_t gbsp_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBSP_H */

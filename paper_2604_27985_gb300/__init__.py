@@ -1,0 +1,18 @@
+"""GB300-native CSR SpMM and SDDMM.
+
+The compute path is libgbsp.so (hand-written CUDA for sm_103a behind the C ABI of
+include/gbsp.h); this package is its thin Python binding.  Importing it fails loudly when
+the library is not built: there is no CPU fallback.
+"""
+from ._lib import GbspError, LIB_PATH  # noqa: F401
+from .ops import (  # noqa: F401
+    csr_validate,
+    launch_count,
+    quantize_bf16,
+    quantize_e4m3_rows,
+    sddmm,
+    sddmm_csr,
+    sm_count,
+    spmm,
+    spmm_csr,
+)

@@ -1,0 +1,153 @@
+// Internal helpers shared by the library's translation units (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include "gbsp.h"
+
+#define GBSP_EXPORT extern "C" __attribute__((visibility("default")))
+
+namespace gbsp {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Records a failure for gbsp_get_last_error / gbsp_last_error_message and returns status.
+int fail(int status, const char *fmt, ...);
+// Clears the per-thread error record and returns GBSP_OK.
+int ok();
+// Adds n to the process-wide count of kernels launched by the library.
+void count_launches(int n);
+// Converts a pending launch error into GBSP_ERR_CUDA (with the CUDA message).
+int check_launch(const char *what);
+// SM count of the current device (cached per device).
+int sm_count();
+// Stream-ordered scratch from a library-owned pool that keeps its memory between calls.
+int scratch_alloc(void **ptr, size_t bytes, cudaStream_t s);
+void scratch_free(void *ptr, cudaStream_t s);
+
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+inline int next_pow2(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// ---- element types ----------------------------------------------------------------------
+// Each dense element type is read 16 bytes at a time (one 128-bit load per lane): V
+// elements per vector.  A-values of the same type give one FP32 coefficient per nonzero.
+
+struct F32 {
+    using stored = float;
+    static constexpr int V = 4;
+    static constexpr int dtype = GBSP_F32;
+    __device__ __forceinline__ static void unpack(const uint4 &r, float (&o)[4]) {
+        o[0] = __uint_as_float(r.x);
+        o[1] = __uint_as_float(r.y);
+        o[2] = __uint_as_float(r.z);
+        o[3] = __uint_as_float(r.w);
+    }
+    __device__ __forceinline__ static float value(float v) { return v; }
+    __device__ __forceinline__ static float scalar(const stored *p) { return *p; }
+};
+
+struct BF16 {
+    using stored = uint16_t;
+    static constexpr int V = 8;
+    static constexpr int dtype = GBSP_BF16;
+    __device__ __forceinline__ static void unpack(const uint4 &r, float (&o)[8]) {
+        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            o[2 * i] = __uint_as_float(w[i] << 16);
+            o[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+        }
+    }
+    __device__ __forceinline__ static float value(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+    __device__ __forceinline__ static float scalar(const stored *p) { return value(*p); }
+};
+
+struct E4M3 {
+    using stored = uint8_t;
+    static constexpr int V = 16;
+    static constexpr int dtype = GBSP_E4M3;
+    __device__ __forceinline__ static float2 pair(uint16_t two) {
+        __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)two, __NV_E4M3);
+        return __half22float2(*reinterpret_cast<__half2 *>(&h));
+    }
+    __device__ __forceinline__ static void unpack(const uint4 &r, float (&o)[16]) {
+        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float2 a = pair((uint16_t)(w[i] & 0xffffu));
+            float2 b = pair((uint16_t)(w[i] >> 16));
+            o[4 * i] = a.x;
+            o[4 * i + 1] = a.y;
+            o[4 * i + 2] = b.x;
+            o[4 * i + 3] = b.y;
+        }
+    }
+    __device__ __forceinline__ static float value(uint8_t q) {
+        __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)q, __NV_E4M3);
+        return __half2float(*reinterpret_cast<__half *>(&h));
+    }
+    __device__ __forceinline__ static float scalar(const stored *p) { return value(*p); }
+};
+
+// Streaming (read-once) loads: indices and values are touched once, so keep them from
+// displacing the gathered dense rows in L1 / L2.
+__device__ __forceinline__ int ld_stream(const int32_t *p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream(const float *p) { return __ldcs(p); }
+__device__ __forceinline__ uint16_t ld_stream(const uint16_t *p) { return __ldcs(reinterpret_cast<const unsigned short *>(p)); }
+__device__ __forceinline__ uint8_t ld_stream(const uint8_t *p) { return __ldcs(reinterpret_cast<const unsigned char *>(p)); }
+
+// Gathered dense rows: read-only path, 16 bytes per lane.
+__device__ __forceinline__ uint4 ld_gather16(const void *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
+
+// ---- launch descriptors -------------------------------------------------------------------
+
+struct SpmmProblem {
+    int32_t M, K, N;
+    int64_t nnz;  // -1 when the caller did not say (read on the device where needed)
+    const int32_t *rowptr, *colidx;
+    const void *vals;
+    const float *a_scale;  // E4M3 per-row scale of A (s_i), else null
+    const void *B;
+    int64_t ldb;
+    const float *b_scale;  // E4M3 per-row scale of B (t_k), else null
+    float *C;
+    int64_t ldc;
+    int dtype;
+};
+
+struct SddmmProblem {
+    int32_t M, N, Kd;
+    int64_t nnz;
+    const int32_t *rowptr, *colidx;
+    const float *svals;
+    const void *X;
+    int64_t ldx;
+    const float *x_scale;
+    const void *Y;
+    int64_t ldy;
+    const float *y_scale;
+    float *out;
+    int dtype;  // dtype of X and Y
+};
+
+// Per-element-type launchers (one translation unit each).
+template <class EL>
+int launch_spmm_typed(const SpmmProblem &p, int variant, int unroll, int ctas_per_sm, cudaStream_t s);
+template <class EL>
+int launch_sddmm_typed(const SddmmProblem &p, int variant, cudaStream_t s);
+
+int launch_spmm(const SpmmProblem &p, int variant, int unroll, int ctas_per_sm, cudaStream_t s);
+int launch_sddmm(const SddmmProblem &p, int variant, int unroll, cudaStream_t s);
+int launch_validate(const gbsp_csr &A, unsigned long long *d_count, cudaStream_t s);
+int launch_quant_bf16(const float *x, uint16_t *out, int64_t n, cudaStream_t s);
+int launch_quant_e4m3_rows(const float *x, const int32_t *rowptr, int64_t nrows, int64_t ncols,
+                           int64_t ld, uint8_t *q, float *scale, cudaStream_t s);
+
+}  // namespace gbsp

@@ -1,0 +1,276 @@
+// SpMM kernels (Eq. 1): C[i, :] = sum over the stored entries p of row i of a_p * B[colidx[p], :].
+//
+// Lane layout shared by every vectorised kernel: a warp splits into G = 32 / LPN groups
+// of LPN lanes.  One group takes one nonzero at a time; each of its lanes gathers VPL
+// 16-byte vectors (EL::V elements each) of the B row colidx[p], so a group covers
+// LPN * VPL * EL::V columns of one column tile.  U gathers are issued per lane before
+// any of them is consumed, so a warp keeps U * G row loads in flight.  Column indices and
+// coefficients are read 32 at a time with one coalesced load per lane and handed to the
+// groups by warp shuffles; the next 32 are prefetched while the current ones are used.
+#pragma once
+
+#include "common.cuh"
+
+namespace gbsp {
+namespace spmm_detail {
+
+// Coefficient of stored entry p: the A value as FP32; for E4M3 it also folds in the
+// per-row scale t_k of the gathered B row (the row scale s_i of A is applied at the end).
+template <class EL>
+__device__ __forceinline__ float coef(const SpmmProblem &P, int64_t p, int c) {
+    const typename EL::stored *vals = static_cast<const typename EL::stored *>(P.vals);
+    float a = EL::value(ld_stream(vals + p));
+    if (EL::dtype == GBSP_E4M3) a *= __ldg(P.b_scale + c);
+    return a;
+}
+
+template <class EL, int LPN, int VPL, int U>
+__device__ __forceinline__ void gather_range(const SpmmProblem &P, int64_t p0, int64_t p1,
+                                             float (&acc)[VPL][EL::V], int lane, int col_base) {
+    constexpr int G = 32 / LPN;
+    static_assert(G * U <= 32, "a chunk of 32 nonzeros must hold whole steps");
+    const int sub = lane / LPN;
+    const char *B = static_cast<const char *>(P.B);
+    const int64_t ldb_bytes = P.ldb * (int64_t)sizeof(typename EL::stored);
+    bool colok[VPL];
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) colok[v] = col_base + v * LPN * EL::V < P.N;
+
+    int c = 0;
+    float a = 0.f;
+    int64_t base = p0;
+    if (base + lane < p1) {
+        c = ld_stream(P.colidx + base + lane);
+        a = coef<EL>(P, base + lane, c);
+    }
+    while (base < p1) {
+        const int64_t nb = base + 32;
+        int c2 = 0;
+        float a2 = 0.f;
+        if (nb + lane < p1) {
+            c2 = ld_stream(P.colidx + nb + lane);
+            a2 = coef<EL>(P, nb + lane, c2);
+        }
+        const int cnt = (int)min((int64_t)32, p1 - base);
+#pragma unroll 1
+        for (int q = 0; q < cnt; q += G * U) {
+            float aj[U];
+            uint4 raw[U][VPL];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int idx = q + u * G + sub;
+                const int cj = __shfl_sync(FULL, c, idx);
+                aj[u] = __shfl_sync(FULL, a, idx);
+                const bool ok = idx < cnt;
+                const char *row = B + (int64_t)cj * ldb_bytes;
+#pragma unroll
+                for (int v = 0; v < VPL; ++v) {
+                    raw[u][v] = make_uint4(0, 0, 0, 0);
+                    if (ok && colok[v])
+                        raw[u][v] = ld_gather16(row + (int64_t)(col_base + v * LPN * EL::V) *
+                                                          (int64_t)sizeof(typename EL::stored));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+#pragma unroll
+                for (int v = 0; v < VPL; ++v) {
+                    float f[EL::V];
+                    EL::unpack(raw[u][v], f);
+#pragma unroll
+                    for (int k = 0; k < EL::V; ++k) acc[v][k] = fmaf(aj[u], f[k], acc[v][k]);
+                }
+            }
+        }
+        base = nb;
+        c = c2;
+        a = a2;
+    }
+}
+
+// Sums the G group partials (xor butterfly across groups) so every group holds the row.
+template <class EL, int LPN, int VPL>
+__device__ __forceinline__ void reduce_groups(float (&acc)[VPL][EL::V]) {
+#pragma unroll
+    for (int off = LPN; off < 32; off <<= 1)
+#pragma unroll
+        for (int v = 0; v < VPL; ++v)
+#pragma unroll
+            for (int k = 0; k < EL::V; ++k) acc[v][k] += __shfl_xor_sync(FULL, acc[v][k], off);
+}
+
+template <class EL, int LPN, int VPL>
+__device__ __forceinline__ void store_row(float *dst_row, const float (&acc)[VPL][EL::V], int lane,
+                                          int col_base, int N, float scale) {
+    if (lane >= LPN) return;
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+        const int col = col_base + v * LPN * EL::V;
+        if (col < N) {
+#pragma unroll
+            for (int k = 0; k < EL::V; k += 4)
+                __stcs(reinterpret_cast<float4 *>(dst_row + col + k),
+                       make_float4(acc[v][k] * scale, acc[v][k + 1] * scale, acc[v][k + 2] * scale,
+                                   acc[v][k + 3] * scale));
+        }
+    }
+}
+
+template <class EL>
+__device__ __forceinline__ float row_scale(const SpmmProblem &P, int row) {
+    return EL::dtype == GBSP_E4M3 ? __ldg(P.a_scale + row) : 1.0f;
+}
+
+// One warp per row; blockIdx.y is the column tile.
+template <class EL, int LPN, int VPL, int U>
+__global__ void __launch_bounds__(256) spmm_rowsplit_kernel(const SpmmProblem P) {
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= P.M) return;
+    const int col_base = blockIdx.y * (LPN * VPL * EL::V) + (lane % LPN) * EL::V;
+    float acc[VPL][EL::V];
+#pragma unroll
+    for (int v = 0; v < VPL; ++v)
+#pragma unroll
+        for (int k = 0; k < EL::V; ++k) acc[v][k] = 0.f;
+    gather_range<EL, LPN, VPL, U>(P, __ldg(P.rowptr + row), __ldg(P.rowptr + row + 1), acc, lane, col_base);
+    reduce_groups<EL, LPN, VPL>(acc);
+    store_row<EL, LPN, VPL>(P.C + (int64_t)row * P.ldc, acc, lane, col_base, P.N, row_scale<EL>(P, row));
+}
+
+// Merge-path coordinate of diagonal d over the two lists "row ends" (rowptr[1..M]) and
+// "stored entries" (0..nnz-1): the number x of rows fully consumed, with y = d - x
+// entries consumed.  Row end i precedes entry j exactly when rowptr[i + 1] <= j.
+// The warp evaluates 32 probes per round (a 33-ary search), then settles the last <= 32.
+__device__ __forceinline__ int merge_search(const int32_t *rowptr, int M, int64_t nnz, int64_t d, int lane) {
+    int64_t lo = d - nnz > 0 ? d - nnz : 0;
+    int64_t hi = d < M ? d : M;
+    while (hi - lo > 32) {
+        const int64_t span = hi - lo;
+        const int64_t probe = lo + (span * (lane + 1)) / 33;
+        const bool t = (int64_t)__ldg(rowptr + probe + 1) + probe + 1 <= d;
+        const int k = __popc(__ballot_sync(FULL, t));
+        const int64_t new_lo = k == 0 ? lo : lo + (span * k) / 33 + 1;
+        const int64_t new_hi = k == 32 ? hi : lo + (span * (k + 1)) / 33;
+        lo = new_lo;
+        hi = new_hi;
+    }
+    const int64_t x = lo + lane;
+    const bool t = x < hi && (int64_t)__ldg(rowptr + x + 1) + x + 1 <= d;
+    return (int)(lo + __popc(__ballot_sync(FULL, t)));
+}
+
+// nnz-balanced split: warp w takes the items [w * ipw, (w + 1) * ipw) of the merge path
+// (M row ends + nnz entries).  Rows that end inside the range are written directly; the
+// partial sum of the row still open at the range end goes to the carry arrays and is
+// added by spmm_merge_fixup_kernel.  The grid is fixed on the host, nnz is read on the
+// device, so the launch needs no host-side knowledge of the matrix.
+template <class EL, int LPN, int VPL, int U>
+__global__ void __launch_bounds__(256) spmm_merge_kernel(const SpmmProblem P, int32_t *carry_row,
+                                                         float *carry_val, int nwarps) {
+    constexpr int TW = LPN * VPL * EL::V;
+    const int lane = threadIdx.x & 31;
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int col_base = blockIdx.y * TW + (lane % LPN) * EL::V;
+    const int64_t nnz = __ldg(P.rowptr + P.M);
+    const int64_t total = (int64_t)P.M + nnz;
+    const int64_t ipw = (total + nwarps - 1) / nwarps;
+    const int64_t d0 = min((int64_t)w * ipw, total);
+    const int64_t d1 = min(d0 + ipw, total);
+    const int x0 = merge_search(P.rowptr, P.M, nnz, d0, lane);
+    const int x1 = merge_search(P.rowptr, P.M, nnz, d1, lane);
+    int64_t p = d0 - x0;
+    const int64_t y1 = d1 - x1;
+    float acc[VPL][EL::V];
+#pragma unroll
+    for (int v = 0; v < VPL; ++v)
+#pragma unroll
+        for (int k = 0; k < EL::V; ++k) acc[v][k] = 0.f;
+    for (int row = x0; row < x1; ++row) {
+        const int64_t e = __ldg(P.rowptr + row + 1);
+        gather_range<EL, LPN, VPL, U>(P, p, e, acc, lane, col_base);
+        reduce_groups<EL, LPN, VPL>(acc);
+        store_row<EL, LPN, VPL>(P.C + (int64_t)row * P.ldc, acc, lane, col_base, P.N, row_scale<EL>(P, row));
+#pragma unroll
+        for (int v = 0; v < VPL; ++v)
+#pragma unroll
+            for (int k = 0; k < EL::V; ++k) acc[v][k] = 0.f;
+        p = e;
+    }
+    gather_range<EL, LPN, VPL, U>(P, p, y1, acc, lane, col_base);
+    reduce_groups<EL, LPN, VPL>(acc);
+    float *cv = carry_val + ((int64_t)blockIdx.y * nwarps + w) * TW;
+    if (lane < LPN) {
+#pragma unroll
+        for (int v = 0; v < VPL; ++v)
+#pragma unroll
+            for (int k = 0; k < EL::V; k += 4)
+                *reinterpret_cast<float4 *>(cv + (lane + v * LPN) * EL::V + k) =
+                    make_float4(acc[v][k], acc[v][k + 1], acc[v][k + 2], acc[v][k + 3]);
+    }
+    if (lane == 0 && blockIdx.y == 0) carry_row[w] = (d0 < d1 && x1 < P.M) ? x1 : -1;
+}
+
+// Adds the carries: the first warp of each run of equal carry rows sums the run in warp
+// order (deterministic) and adds it, times the row scale, into C.
+template <class EL>
+__global__ void __launch_bounds__(256) spmm_merge_fixup_kernel(const SpmmProblem P, const int32_t *carry_row,
+                                                               const float *carry_val, int nwarps, int TW) {
+    const int lane = threadIdx.x & 31;
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= nwarps) return;
+    const int r = carry_row[w];
+    if (r < 0 || (w > 0 && carry_row[w - 1] == r)) return;
+    const float sc = row_scale<EL>(P, r);
+    for (int col = lane; col < TW; col += 32) {
+        const int gcol = blockIdx.y * TW + col;
+        if (gcol >= P.N) break;
+        float s = 0.f;
+        for (int w2 = w; w2 < nwarps && carry_row[w2] == r; ++w2)
+            s += carry_val[((int64_t)blockIdx.y * nwarps + w2) * TW + col];
+        float *dst = P.C + (int64_t)r * P.ldc + gcol;
+        *dst += s * sc;
+    }
+}
+
+// Unvectorised form for any width and alignment: one warp per row, lane l owns columns
+// l, l + 32, l + 64, l + 96 of a 128-column pass.
+template <class EL>
+__global__ void __launch_bounds__(256) spmm_scalar_kernel(const SpmmProblem P) {
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= P.M) return;
+    const int64_t p0 = __ldg(P.rowptr + row), p1 = __ldg(P.rowptr + row + 1);
+    const typename EL::stored *B = static_cast<const typename EL::stored *>(P.B);
+    const float sc = row_scale<EL>(P, row);
+    for (int c0 = blockIdx.y * 128; c0 < P.N; c0 += gridDim.y * 128) {
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int64_t base = p0; base < p1; base += 32) {
+            int c = 0;
+            float a = 0.f;
+            if (base + lane < p1) {
+                c = ld_stream(P.colidx + base + lane);
+                a = coef<EL>(P, base + lane, c);
+            }
+            const int cnt = (int)min((int64_t)32, p1 - base);
+            for (int j = 0; j < cnt; ++j) {
+                const int cj = __shfl_sync(FULL, c, j);
+                const float aj = __shfl_sync(FULL, a, j);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int col = c0 + lane + 32 * t;
+                    if (col < P.N) acc[t] = fmaf(aj, EL::scalar(B + (int64_t)cj * P.ldb + col), acc[t]);
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int col = c0 + lane + 32 * t;
+            if (col < P.N) P.C[(int64_t)row * P.ldc + col] = acc[t] * sc;
+        }
+    }
+}
+
+}  // namespace spmm_detail
+
+}  // namespace gbsp

@@ -1,0 +1,144 @@
+"""Torch-tensor front end of the C ABI: same names as the entry points, marshalling only.
+
+Every function takes CUDA tensors, passes their device pointers and the current torch
+stream (or the one given) to libgbsp.so, and returns the output tensor.  No arithmetic of
+SpMM / SDDMM happens here; PyTorch only owns the memory and the stream.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import BF16, E4M3, F32, VARIANTS, Csr, Dense, Opts, check, lib
+
+_DT = {torch.float32: F32, torch.bfloat16: BF16, torch.uint8: E4M3}
+if hasattr(torch, "float8_e4m3fn"):
+    _DT[torch.float8_e4m3fn] = E4M3
+
+
+def _dtype(t: torch.Tensor) -> int:
+    try:
+        return _DT[t.dtype]
+    except KeyError:
+        raise TypeError(f"unsupported dtype {t.dtype}") from None
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensors must live on a CUDA device")
+    return t.data_ptr() or None
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ld(t: torch.Tensor) -> int:
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("dense operands must be 2-D with unit column stride")
+    return t.stride(0) if t.shape[0] > 1 else max(t.stride(0), t.shape[1])
+
+
+def _csr(rowptr, colidx, vals, ncols, scale=None) -> Csr:
+    for t, name in ((rowptr, "rowptr"), (colidx, "colidx")):
+        if t.dtype != torch.int32 or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous int32 tensor")
+    if not vals.is_contiguous():
+        raise ValueError("vals must be contiguous")
+    return Csr(rowptr.numel() - 1, int(ncols), colidx.numel(), _ptr(rowptr), _ptr(colidx), _ptr(vals),
+               _ptr(scale), _dtype(vals))
+
+
+def _dense(t: torch.Tensor, scale=None) -> Dense:
+    return Dense(_ptr(t), t.shape[0], t.shape[1], _ld(t), _ptr(scale), _dtype(t))
+
+
+def _opts(variant="auto", validate=False, unroll=0, ctas_per_sm=0) -> Opts:
+    return Opts(VARIANTS[variant] if isinstance(variant, str) else int(variant), int(bool(validate)),
+                int(unroll), int(ctas_per_sm))
+
+
+def spmm_csr(rowptr, colidx, vals, B, C, M, K, N) -> None:
+    """The plain FP32 entry point (legacy default stream): C = A B, Eq. 1."""
+    check(lib.spmm_csr(_ptr(rowptr), _ptr(colidx), _ptr(vals), _ptr(B), _ptr(C), int(M), int(K), int(N)))
+
+
+def sddmm_csr(rowptr, colidx, svals, X, Y, out, M, N, Kd) -> None:
+    """The plain FP32 entry point (legacy default stream): out = S o (X Y^T), Eq. 2."""
+    check(lib.sddmm_csr(_ptr(rowptr), _ptr(colidx), _ptr(svals), _ptr(X), _ptr(Y), _ptr(out), int(M), int(N),
+                        int(Kd)))
+
+
+def spmm(rowptr, colidx, vals, B, out=None, *, a_scale=None, b_scale=None, variant="auto", unroll=0,
+         ctas_per_sm=0, validate=False, stream=None) -> torch.Tensor:
+    """C = A B (Eq. 1) through spmm_csr_ex; returns the FP32 M x N result."""
+    M = rowptr.numel() - 1
+    if out is None:
+        out = torch.empty((M, B.shape[1]), dtype=torch.float32, device=B.device)
+    A = _csr(rowptr, colidx, vals, B.shape[0], a_scale)
+    b, c = _dense(B, b_scale), _dense(out)
+    o = _opts(variant, validate, unroll, ctas_per_sm)
+    check(lib.spmm_csr_ex(ctypes.byref(A), ctypes.byref(b), ctypes.byref(c), ctypes.byref(o), _stream(stream)))
+    return out
+
+
+def sddmm(rowptr, colidx, svals, X, Y, out=None, *, x_scale=None, y_scale=None, variant="auto",
+          validate=False, stream=None) -> torch.Tensor:
+    """out[p] = s_p <X_i, Y_j> (Eq. 2) through sddmm_csr_ex; returns FP32 out[nnz]."""
+    if out is None:
+        out = torch.empty(colidx.numel(), dtype=torch.float32, device=X.device)
+    S = _csr(rowptr, colidx, svals, Y.shape[0])
+    x, y = _dense(X, x_scale), _dense(Y, y_scale)
+    o = _opts(variant, validate)
+    check(lib.sddmm_csr_ex(ctypes.byref(S), ctypes.byref(x), ctypes.byref(y), _ptr(out), ctypes.byref(o),
+                           _stream(stream)))
+    return out
+
+
+def csr_validate(rowptr, colidx, ncols, stream=None) -> int:
+    """Number of CSR violations (0 for a valid matrix); synchronises the stream."""
+    A = Csr(rowptr.numel() - 1, int(ncols), colidx.numel(), _ptr(rowptr), _ptr(colidx), _ptr(colidx) or 1,
+            None, F32)
+    bad = ctypes.c_int64(0)
+    st = lib.gbsp_csr_validate(ctypes.byref(A), _stream(stream), ctypes.byref(bad))
+    if st not in (_lib.GBSP_OK, -2):
+        check(st)
+    return int(bad.value)
+
+
+def quantize_bf16(x: torch.Tensor, stream=None) -> torch.Tensor:
+    """bfloat16 round-to-nearest-even of an FP32 tensor (library kernel)."""
+    x = x.contiguous()
+    out = torch.empty(x.shape, dtype=torch.bfloat16, device=x.device)
+    check(lib.gbsp_quantize_bf16(_ptr(x), _ptr(out), x.numel(), _stream(stream)))
+    return out
+
+
+def quantize_e4m3_rows(x: torch.Tensor, rowptr: torch.Tensor | None = None, stream=None):
+    """Per-row scaled E4M3 codes (uint8) and FP32 row scales (library kernel).  Rows are
+    CSR segments of the 1-D ``x`` when ``rowptr`` is given, else the rows of 2-D ``x``."""
+    x = x.contiguous()
+    q = torch.empty(x.shape, dtype=torch.uint8, device=x.device)
+    if rowptr is None:
+        nrows, ncols, ld = x.shape[0], x.shape[1], x.shape[1]
+    else:
+        nrows, ncols, ld = rowptr.numel() - 1, 0, 0
+    scale = torch.empty(nrows, dtype=torch.float32, device=x.device)
+    check(lib.gbsp_quantize_e4m3_rows(_ptr(x), _ptr(rowptr), nrows, ncols, ld, _ptr(q), _ptr(scale),
+                                      _stream(stream)))
+    return q, scale
+
+
+def sm_count() -> int:
+    return int(lib.gbsp_device_sm_count())
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(lib.gbsp_launch_count())
