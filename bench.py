@@ -163,13 +163,56 @@ def kernel_traffic():
             t = json.load(f)
     except Exception:
         return None, None
-    h = hashlib.sha256()
-    for name in t.get("sources", []):
-        with open(os.path.join(ROOT, name), "rb") as f:
-            h.update(f.read())
-    if h.hexdigest() != t.get("sources_sha256"):
+    try:
+        if sources_sha256(t.get("sources", [])) != t.get("sources_sha256"):
+            return None, None
+    except OSError:
         return None, None
     return t.get("spmm_bytes_per_launch"), t.get("sddmm_bytes_per_launch")
+
+
+TRAFFIC_SOURCES = ["paper_2604_27985_gb300/csrc/common.cuh", "paper_2604_27985_gb300/csrc/spmm_kernels.cuh",
+                   "paper_2604_27985_gb300/csrc/spmm_launch.cuh", "paper_2604_27985_gb300/csrc/sddmm_kernels.cuh",
+                   "paper_2604_27985_gb300/csrc/sddmm.cu", "paper_2604_27985_gb300/csrc/api.cu"]
+
+
+def sources_sha256(names):
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def write_traffic(report, spmm_re, sddmm_re):
+    """Stores per-launch DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the
+    SpMM and SDDMM kernels from an ncu report in profiles/traffic.json, stamped with the
+    sha256 of the kernel sources: bench lines carry them only while the kernels are
+    unchanged."""
+    import csv
+    import io
+    import re
+
+    out = subprocess.run(["ncu", "-i", report, "--page", "raw", "--csv"], capture_output=True, text=True).stdout
+    rows = list(csv.reader(io.StringIO(out)))
+    hdr, units = rows[0], rows[1]
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+
+    def per_launch(pattern):
+        vals = []
+        for r in rows[2:]:
+            d = dict(zip(hdr, r))
+            if re.search(pattern, d["Kernel Name"]):
+                vals.append(sum(float(d[m].replace(",", "")) * scale[units[hdr.index(m)]]
+                                for m in ("dram__bytes_read.sum", "dram__bytes_write.sum")))
+        return sum(vals) / len(vals) if vals else None
+
+    t = {"report": os.path.basename(report), "sources": TRAFFIC_SOURCES,
+         "sources_sha256": sources_sha256(TRAFFIC_SOURCES),
+         "spmm_bytes_per_launch": per_launch(spmm_re), "sddmm_bytes_per_launch": per_launch(sddmm_re)}
+    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
+        json.dump(t, f, indent=1)
+    print(json.dumps(t))
 
 
 def run_ours(args):
@@ -399,7 +442,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--write-traffic", nargs=3, metavar=("REPORT", "SPMM_RE", "SDDMM_RE"),
+                    help="store per-launch DRAM bytes from an ncu report and exit")
     args = ap.parse_args()
+    if args.write_traffic:
+        write_traffic(*args.write_traffic)
+        return
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
     if args.impl == "reference":
