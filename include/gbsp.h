@@ -139,6 +139,27 @@ int gbsp_quantize_bf16(const float *x, uint16_t *out, int64_t n, void *stream);
 int gbsp_quantize_e4m3_rows(const float *x, const int32_t *rowptr, int64_t nrows, int64_t ncols,
                             int64_t ld, uint8_t *q, float *scale, void *stream);
 
+/* ---- allocation-free variant ---------------------------------------------------------- */
+
+/* The paper has no counterpart of this entry point.  It serves callers that must not
+ * allocate device memory during a call: a process whose HBM is already handed out by
+ * another allocator (so an allocation can fail at call time), a latency-bound loop that
+ * cannot absorb an allocation, code recorded into a CUDA graph that must hold no
+ * allocation nodes.
+ * FP32 SpMM with the meaning of spmm_csr (Eq. 1; rowptr, colidx, vals, B, C device; B and
+ * C with ld = N; C overwritten), on the given stream, through the merge-path kernels.
+ * Their carry buffers live in one fixed 4 MiB device array owned by the library, which
+ * every GPU that loads the library holds until the process exits; nothing is allocated.
+ * Limits: N <= 1024 and a multiple of 4, B and C 16-byte aligned; a larger N returns
+ * GBSP_ERR_INVALID_ARG, misalignment GBSP_ERR_ALIGN.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current: make that
+ * first call before any stream capture.  All calls share the one array, so calls that can
+ * overlap on the GPU (unordered streams) race and must be serialised by the caller.  Each
+ * call writes every scratch element before reading it, so what a previous call left there
+ * does not matter. */
+int spmm_csr_noalloc(const int32_t *rowptr, const int32_t *colidx, const float *vals, const float *B,
+                     float *C, int64_t M, int64_t K, int64_t N, void *stream);
+
 /* ---- errors ------------------------------------------------------------------------ */
 
 const char *gbsp_status_string(int status);

@@ -15,4 +15,5 @@ from .ops import (  # noqa: F401
     sm_count,
     spmm,
     spmm_csr,
+    spmm_csr_noalloc,
 )

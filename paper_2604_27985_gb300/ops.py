@@ -69,6 +69,13 @@ def spmm_csr(rowptr, colidx, vals, B, C, M, K, N) -> None:
     check(lib.spmm_csr(_ptr(rowptr), _ptr(colidx), _ptr(vals), _ptr(B), _ptr(C), int(M), int(K), int(N)))
 
 
+def spmm_csr_noalloc(rowptr, colidx, vals, B, C, M, K, N, stream=None) -> None:
+    """FP32 SpMM (Eq. 1) that allocates nothing: the merge-path carries live in a fixed
+    device array of the library (for callers that cannot allocate during a call)."""
+    check(lib.spmm_csr_noalloc(_ptr(rowptr), _ptr(colidx), _ptr(vals), _ptr(B), _ptr(C), int(M), int(K), int(N),
+                               _stream(stream)))
+
+
 def sddmm_csr(rowptr, colidx, svals, X, Y, out, M, N, Kd) -> None:
     """The plain FP32 entry point (legacy default stream): out = S o (X Y^T), Eq. 2."""
     check(lib.sddmm_csr(_ptr(rowptr), _ptr(colidx), _ptr(svals), _ptr(X), _ptr(Y), _ptr(out), int(M), int(N),
