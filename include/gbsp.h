@@ -88,6 +88,7 @@ typedef struct {
     int32_t validate;  /* nonzero: run gbsp_csr_validate first (synchronises the stream) */
     int32_t unroll;    /* 0 = default; else gathers in flight per lane (1, 2, 4 or 8) */
     int32_t ctas_per_sm; /* merge-path grid: CTAs per SM (0 = default) */
+    int32_t vecs;      /* 0 = default; else 16-byte vectors each lane moves per row (1, 2 or 4) */
 } gbsp_opts;
 
 /* ---- plain FP32 forms (spec signatures), legacy default stream --------------- */
@@ -138,6 +139,55 @@ int gbsp_quantize_bf16(const float *x, uint16_t *out, int64_t n, void *stream);
  * otherwise nrows dense rows of ncols entries with leading dimension ld (q uses ld too). */
 int gbsp_quantize_e4m3_rows(const float *x, const int32_t *rowptr, int64_t nrows, int64_t ncols,
                             int64_t ld, uint8_t *q, float *scale, void *stream);
+
+/* ---- condensed-tile tensor-core plan (BF16) ----------------------------------------------- */
+
+/* A plan splits a BF16 CSR matrix A into dense 16 x 8 blocks (aligned; at least `threshold`
+ * stored entries, default 16 when threshold < 1) and a residual CSR.  Executing it computes
+ * C = A B (Eq. 1) as: residual SpMM through the CSR kernels (which writes C), then, for each
+ * 16-row window holding dense blocks, a tcgen05 MMA of the window's condensed 16 x Kc tile
+ * with the Kc gathered rows of B (BF16 operands, FP32 accumulation in tensor memory), added
+ * into C.  The plan keeps its own device copy of everything it needs; A may be freed after
+ * creation.  Requirements: A->dtype BF16 with strictly increasing column indices in every
+ * row (GBSP_ERR_UNSUPPORTED otherwise); at execution B BF16 (K x N) and C FP32 (M x N) with
+ * 64 <= N <= 512, N and B->ld multiples of 8 and B 16-byte aligned when any window is dense.
+ * residual_opts (may be NULL) chooses the residual kernel.  gbsp_plan_create synchronises
+ * the stream; gbsp_plan_execute is asynchronous and may be repeated with new B and C.
+ * Device-side waits in the tensor-core kernel give up after about a second and record it;
+ * gbsp_plan_check (synchronous) returns GBSP_ERR_TIMEOUT if any did.
+ * gbsp_plan_info fills info[0..4] = {dense windows, dense blocks (padded to multiples of 8
+ * per window), entries inside dense blocks, residual entries, threshold}. */
+typedef struct gbsp_plan gbsp_plan;
+int gbsp_plan_create(const gbsp_csr *A, int32_t threshold, const gbsp_opts *residual_opts, void *stream,
+                     gbsp_plan **out);
+int gbsp_plan_execute(const gbsp_plan *plan, const gbsp_dense *B, gbsp_dense *C, void *stream);
+int gbsp_plan_info(const gbsp_plan *plan, int64_t *info, int n);
+int gbsp_plan_check(const gbsp_plan *plan, void *stream);
+void gbsp_plan_destroy(gbsp_plan *plan);
+
+/* ---- batched graph chain (one persistent launch in a CUDA graph) ---------------------------- */
+
+/* For each graph g of a batch of G (arrays of G host-side descriptors, device data):
+ *   E_g = S_g o (H_g H_g^T) on the pattern of S_g      (Eq. 2 with X = Y = H_g)
+ *   O_g = E_g H_g                                       (Eq. 1 with the values E_g)
+ * S_g: square FP32 CSR with nnz given; H_g, O_g: BF16 n_g x N_g (N_g a multiple of 8,
+ * at most 256, rows 16-byte aligned); E[g]: device float[nnz_g] in CSR order.  Accumulation
+ * is FP32; O is rounded to BF16 (nearest even).  The plan builds a device work list of row
+ * tiles (about edges_per_tile edges each, default 2048 when <= 0) over all graphs and
+ * records one persistent launch, which takes tiles from an atomic ticket, into a CUDA
+ * graph; gbsp_gnn_plan_execute replays it on the stream (asynchronous).  The plan keeps the
+ * caller's pointers: the data may change between executions, the allocations may not.
+ * gbsp_gnn_plan_create reads every rowptr to the host (synchronises the stream).
+ * gbsp_gnn_plan_info fills {graphs, tiles, rows, edges}.  gnn_sddmm_spmm_batched is the
+ * one-shot form (create, execute, synchronise, destroy). */
+typedef struct gbsp_gnn_plan gbsp_gnn_plan;
+int gbsp_gnn_plan_create(int G, const gbsp_csr *S, const gbsp_dense *H, float *const *E, gbsp_dense *O,
+                         int32_t edges_per_tile, void *stream, gbsp_gnn_plan **out);
+int gbsp_gnn_plan_execute(const gbsp_gnn_plan *plan, void *stream);
+int gbsp_gnn_plan_info(const gbsp_gnn_plan *plan, int64_t *info, int n);
+void gbsp_gnn_plan_destroy(gbsp_gnn_plan *plan);
+int gnn_sddmm_spmm_batched(int G, const gbsp_csr *S, const gbsp_dense *H, float *const *E, gbsp_dense *O,
+                           void *stream);
 
 /* ---- allocation-free variant ---------------------------------------------------------- */
 

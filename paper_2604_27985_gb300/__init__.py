@@ -6,6 +6,9 @@ the library is not built: there is no CPU fallback.
 """
 from ._lib import GbspError, LIB_PATH  # noqa: F401
 from .ops import (  # noqa: F401
+    GnnPlan,
+    gnn_sddmm_spmm_batched,
+    TcPlan,
     csr_validate,
     launch_count,
     quantize_bf16,

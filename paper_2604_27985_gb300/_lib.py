@@ -45,7 +45,7 @@ class Dense(ctypes.Structure):
 
 class Opts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("validate", ctypes.c_int32), ("unroll", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("vecs", ctypes.c_int32)]
 
 
 def _load() -> ctypes.CDLL:
@@ -64,6 +64,16 @@ def _load() -> ctypes.CDLL:
         "gbsp_csr_validate": [ctypes.POINTER(Csr), P, ctypes.POINTER(ctypes.c_int64)],
         "gbsp_quantize_bf16": [P, P, I64, P],
         "gbsp_quantize_e4m3_rows": [P, P, I64, I64, I64, P, P, P],
+        "gbsp_plan_create": [ctypes.POINTER(Csr), ctypes.c_int32, ctypes.POINTER(Opts), P, ctypes.POINTER(P)],
+        "gbsp_plan_execute": [P, ctypes.POINTER(Dense), ctypes.POINTER(Dense), P],
+        "gbsp_plan_info": [P, ctypes.POINTER(I64), I],
+        "gbsp_plan_check": [P, P],
+        "gbsp_gnn_plan_create": [I, ctypes.POINTER(Csr), ctypes.POINTER(Dense), ctypes.POINTER(P),
+                                 ctypes.POINTER(Dense), ctypes.c_int32, P, ctypes.POINTER(P)],
+        "gbsp_gnn_plan_execute": [P, P],
+        "gbsp_gnn_plan_info": [P, ctypes.POINTER(I64), I],
+        "gnn_sddmm_spmm_batched": [I, ctypes.POINTER(Csr), ctypes.POINTER(Dense), ctypes.POINTER(P),
+                                   ctypes.POINTER(Dense), P],
         "gbsp_get_last_error": [],
         "gbsp_device_sm_count": [],
     }
@@ -71,6 +81,10 @@ def _load() -> ctypes.CDLL:
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = I
+    lib.gbsp_gnn_plan_destroy.argtypes = [P]
+    lib.gbsp_gnn_plan_destroy.restype = None
+    lib.gbsp_plan_destroy.argtypes = [P]
+    lib.gbsp_plan_destroy.restype = None
     lib.gbsp_status_string.argtypes = [I]
     lib.gbsp_status_string.restype = ctypes.c_char_p
     lib.gbsp_launch_count.argtypes = []

@@ -83,21 +83,11 @@ void scratch_free(void *ptr, cudaStream_t s) {
     if (ptr) cudaFreeAsync(ptr, s);
 }
 
-int launch_spmm(const SpmmProblem &p, int variant, int unroll, int ctas_per_sm, cudaStream_t s) {
+int launch_sddmm(const SddmmProblem &p, int variant, int vecs, cudaStream_t s) {
     switch (p.dtype) {
-        case GBSP_F32: return launch_spmm_typed<F32>(p, variant, unroll, ctas_per_sm, s);
-        case GBSP_BF16: return launch_spmm_typed<BF16>(p, variant, unroll, ctas_per_sm, s);
-        case GBSP_E4M3: return launch_spmm_typed<E4M3>(p, variant, unroll, ctas_per_sm, s);
-    }
-    return fail(GBSP_ERR_UNSUPPORTED, "spmm: dtype %d", p.dtype);
-}
-
-int launch_sddmm(const SddmmProblem &p, int variant, int unroll, cudaStream_t s) {
-    (void)unroll;
-    switch (p.dtype) {
-        case GBSP_F32: return launch_sddmm_typed<F32>(p, variant, s);
-        case GBSP_BF16: return launch_sddmm_typed<BF16>(p, variant, s);
-        case GBSP_E4M3: return launch_sddmm_typed<E4M3>(p, variant, s);
+        case GBSP_F32: return launch_sddmm_typed<F32>(p, variant, vecs, s);
+        case GBSP_BF16: return launch_sddmm_typed<BF16>(p, variant, vecs, s);
+        case GBSP_E4M3: return launch_sddmm_typed<E4M3>(p, variant, vecs, s);
     }
     return fail(GBSP_ERR_UNSUPPORTED, "sddmm: dtype %d", p.dtype);
 }
@@ -156,6 +146,8 @@ GBSP_EXPORT int spmm_csr_ex(const gbsp_csr *A, const gbsp_dense *B, gbsp_dense *
     gbsp_opts o = opts ? *opts : gbsp_opts{};
     if (o.unroll != 0 && o.unroll != 1 && o.unroll != 2 && o.unroll != 4 && o.unroll != 8)
         return fail(GBSP_ERR_INVALID_ARG, "spmm: unroll must be 0, 1, 2, 4 or 8");
+    if (o.vecs != 0 && o.vecs != 1 && o.vecs != 2 && o.vecs != 4)
+        return fail(GBSP_ERR_INVALID_ARG, "spmm: vecs must be 0, 1, 2 or 4");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (o.validate && A->nnz >= 0) {
         int64_t bad = 0;
@@ -185,7 +177,7 @@ GBSP_EXPORT int spmm_csr_ex(const gbsp_csr *A, const gbsp_dense *B, gbsp_dense *
     p.C = static_cast<float *>(C->data);
     p.ldc = C->ld;
     p.dtype = A->dtype;
-    if ((st = launch_spmm(p, variant, o.unroll, o.ctas_per_sm, s))) return st;
+    if ((st = launch_spmm(p, variant, o.vecs, o.unroll, o.ctas_per_sm, s))) return st;
     return ok();
 }
 
@@ -202,6 +194,8 @@ GBSP_EXPORT int sddmm_csr_ex(const gbsp_csr *S, const gbsp_dense *X, const gbsp_
     if (X->dtype != Y->dtype) return fail(GBSP_ERR_UNSUPPORTED, "sddmm: X and Y must have the same dtype");
     if (S->nnz != 0 && !out) return fail(GBSP_ERR_INVALID_ARG, "sddmm: null out");
     gbsp_opts o = opts ? *opts : gbsp_opts{};
+    if (o.vecs != 0 && o.vecs != 1 && o.vecs != 2 && o.vecs != 4)
+        return fail(GBSP_ERR_INVALID_ARG, "sddmm: vecs must be 0, 1, 2 or 4");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (o.validate && S->nnz >= 0) {
         int64_t bad = 0;
@@ -209,14 +203,13 @@ GBSP_EXPORT int sddmm_csr_ex(const gbsp_csr *S, const gbsp_dense *X, const gbsp_
     }
     if (S->rows == 0 || S->nnz == 0) return ok();
     const int V = elems_per_vec(X->dtype);
-    const bool vec = vec_ok(X) && vec_ok(Y) && X->cols > 0 && X->cols <= 128 * V;
+    const bool vec = vec_ok(X) && vec_ok(Y) && X->cols > 0 && X->cols <= 32 * 16;
     int variant = o.variant;
-    if (variant == GBSP_VARIANT_AUTO || variant == GBSP_VARIANT_MERGE)
-        variant = vec ? GBSP_VARIANT_ROWSPLIT : GBSP_VARIANT_SCALAR;
-    if (variant == GBSP_VARIANT_ROWSPLIT && !vec)
+    if (variant == GBSP_VARIANT_AUTO) variant = vec ? GBSP_VARIANT_ROWSPLIT : GBSP_VARIANT_SCALAR;
+    if ((variant == GBSP_VARIANT_ROWSPLIT || variant == GBSP_VARIANT_MERGE) && !vec)
         return fail(GBSP_ERR_ALIGN, "sddmm: vectorised variant needs 16-byte aligned X and Y, Kd and ld "
-                                    "multiples of %d and Kd <= %d", V, 128 * V);
-    if (variant != GBSP_VARIANT_ROWSPLIT && variant != GBSP_VARIANT_SCALAR)
+                                    "multiples of %d and Kd <= %d", V, 32 * 16);
+    if (variant < GBSP_VARIANT_ROWSPLIT || variant > GBSP_VARIANT_SCALAR)
         return fail(GBSP_ERR_INVALID_ARG, "sddmm: unknown variant %d", variant);
     SddmmProblem p{};
     p.M = (int32_t)S->rows;
@@ -234,7 +227,7 @@ GBSP_EXPORT int sddmm_csr_ex(const gbsp_csr *S, const gbsp_dense *X, const gbsp_
     p.y_scale = Y->row_scale;
     p.out = out;
     p.dtype = X->dtype;
-    if ((st = launch_sddmm(p, variant, o.unroll, s))) return st;
+    if ((st = launch_sddmm(p, variant, o.vecs, s))) return st;
     return ok();
 }
 

@@ -106,6 +106,28 @@ __device__ __forceinline__ uint8_t ld_stream(const uint8_t *p) { return __ldcs(r
 // Gathered dense rows: read-only path, 16 bytes per lane.
 __device__ __forceinline__ uint4 ld_gather16(const void *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
 
+// Merge-path coordinate of diagonal d over the two lists "row ends" (rowptr[1..M]) and
+// "stored entries" (0..nnz-1): the number x of rows fully consumed, with y = d - x
+// entries consumed.  Row end i precedes entry j exactly when rowptr[i + 1] <= j.
+// The warp evaluates 32 probes per round (a 33-ary search), then settles the last <= 32.
+__device__ __forceinline__ int merge_search(const int32_t *rowptr, int M, int64_t nnz, int64_t d, int lane) {
+    int64_t lo = d - nnz > 0 ? d - nnz : 0;
+    int64_t hi = d < M ? d : M;
+    while (hi - lo > 32) {
+        const int64_t span = hi - lo;
+        const int64_t probe = lo + (span * (lane + 1)) / 33;
+        const bool t = (int64_t)__ldg(rowptr + probe + 1) + probe + 1 <= d;
+        const int k = __popc(__ballot_sync(FULL, t));
+        const int64_t new_lo = k == 0 ? lo : lo + (span * k) / 33 + 1;
+        const int64_t new_hi = k == 32 ? hi : lo + (span * (k + 1)) / 33;
+        lo = new_lo;
+        hi = new_hi;
+    }
+    const int64_t x = lo + lane;
+    const bool t = x < hi && (int64_t)__ldg(rowptr + x + 1) + x + 1 <= d;
+    return (int)(lo + __popc(__ballot_sync(FULL, t)));
+}
+
 // ---- launch descriptors -------------------------------------------------------------------
 
 struct SpmmProblem {
@@ -137,14 +159,15 @@ struct SddmmProblem {
     int dtype;  // dtype of X and Y
 };
 
-// Per-element-type launchers (one translation unit each).
+// SpMM launchers: one translation unit per (element type, algorithm).
+template <class EL, int ALGO>
+int launch_spmm_algo(const SpmmProblem &p, int vecs, int unroll, int ctas_per_sm, cudaStream_t s);
 template <class EL>
-int launch_spmm_typed(const SpmmProblem &p, int variant, int unroll, int ctas_per_sm, cudaStream_t s);
-template <class EL>
-int launch_sddmm_typed(const SddmmProblem &p, int variant, cudaStream_t s);
+int launch_sddmm_typed(const SddmmProblem &p, int variant, int vecs, cudaStream_t s);
 
-int launch_spmm(const SpmmProblem &p, int variant, int unroll, int ctas_per_sm, cudaStream_t s);
-int launch_sddmm(const SddmmProblem &p, int variant, int unroll, cudaStream_t s);
+// vecs: 16-byte vectors per lane (0 = default); unroll: gathers in flight per lane.
+int launch_spmm(const SpmmProblem &p, int variant, int vecs, int unroll, int ctas_per_sm, cudaStream_t s);
+int launch_sddmm(const SddmmProblem &p, int variant, int vecs, cudaStream_t s);
 int launch_validate(const gbsp_csr &A, unsigned long long *d_count, cudaStream_t s);
 int launch_quant_bf16(const float *x, uint16_t *out, int64_t n, cudaStream_t s);
 int launch_quant_e4m3_rows(const float *x, const int32_t *rowptr, int64_t nrows, int64_t ncols,

@@ -1,0 +1,319 @@
+// Batched graph chain: for each graph g of a batch,
+//   E_g = S_g o (H_g H_g^T)   on the pattern of S_g   (SDDMM, Eq. 2 with X = Y = H_g)
+//   O_g = E_g H_g                                       (SpMM, Eq. 1 with A's values E_g)
+// with BF16 features H_g (n_g x N_g, N_g a multiple of 8 up to 256), FP32 E_g and
+// accumulation, BF16 O_g (round to nearest even).
+//
+// One persistent launch covers the whole batch: the work list holds tiles of consecutive
+// rows of one graph with about the same number of edges; warps take tiles from an atomic
+// ticket.  Each row is fused: every gathered H_j serves both the dot product with H_i (its
+// edge's E value, reduced across the lane group by an xor butterfly) and the accumulation
+// E_ij * H_j into O_i, so H_j is read once per edge.  The launch (and the ticket reset) is
+// recorded once into a CUDA graph and replayed per execution.
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace gbsp {
+namespace gnn {
+
+struct GraphDesc {
+    const int32_t *rowptr;  // n + 1
+    const int32_t *colidx;  // local column indices
+    const float *svals;
+    const uint16_t *H;  // BF16 n x N, leading dimension ldh
+    uint16_t *O;        // BF16 n x N, leading dimension ldo
+    float *E;           // nnz
+    int64_t ldh, ldo;
+    int32_t n, N;
+};
+
+struct Tile {
+    int32_t graph, row0, row1;
+};
+
+struct GnnArgs {
+    const GraphDesc *graphs;
+    const Tile *tiles;
+    int ntiles;
+    unsigned *ticket;
+};
+
+// One row of one graph with LPN lanes x VPL BF16 vectors (8 features each) per edge.
+template <int LPN, int VPL, int U>
+__device__ __forceinline__ void gnn_row(const GraphDesc &g, int row, int lane) {
+    constexpr int G = 32 / LPN;
+    constexpr int STEP = G * U;
+    static_assert(STEP <= 32 && 32 % STEP == 0, "whole steps per chunk");
+    const int sl = lane % LPN, sub = lane / LPN;
+    bool colok[VPL];
+    float x[VPL][8];
+    const uint4 *Hv = reinterpret_cast<const uint4 *>(g.H) + sl;
+    const int64_t ldv = g.ldh / 8;
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+        colok[v] = (v * LPN + sl) * 8 < g.N;
+        uint4 raw = make_uint4(0, 0, 0, 0);
+        if (colok[v]) raw = __ldg(Hv + (int64_t)row * ldv + v * LPN);
+        BF16::unpack(raw, x[v]);
+    }
+    float acc[VPL][8];
+#pragma unroll
+    for (int v = 0; v < VPL; ++v)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[v][k] = 0.f;
+
+    const int64_t p0 = g.rowptr[row], p1 = g.rowptr[row + 1];
+    int c = 0;
+    float s = 0.f;
+    if (p0 + lane < p1) {
+        c = ld_stream(g.colidx + p0 + lane);
+        s = ld_stream(g.svals + p0 + lane);
+    }
+    for (int64_t base = p0; base < p1; base += 32) {
+        const int64_t nb = base + 32;
+        int c2 = 0;
+        float s2 = 0.f;
+        if (nb + lane < p1) {
+            c2 = ld_stream(g.colidx + nb + lane);
+            s2 = ld_stream(g.svals + nb + lane);
+        }
+        const int cnt = (int)min((int64_t)32, p1 - base);
+#pragma unroll 1
+        for (int q = 0; q < cnt; q += STEP) {
+            uint4 raw[U][VPL];
+            float sj[U];
+            bool ok[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int idx = q + u * G + sub;
+                const int cj = __shfl_sync(FULL, c, idx);
+                sj[u] = __shfl_sync(FULL, s, idx);
+                ok[u] = idx < cnt;
+                const uint4 *rp = Hv + (int64_t)cj * ldv;
+#pragma unroll
+                for (int v = 0; v < VPL; ++v)
+                    raw[u][v] = (ok[u] && colok[v]) ? __ldg(rp + v * LPN) : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                float f[VPL][8];
+                float dot = 0.f;
+#pragma unroll
+                for (int v = 0; v < VPL; ++v) {
+                    BF16::unpack(raw[u][v], f[v]);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) dot = fmaf(x[v][k], f[v][k], dot);
+                }
+#pragma unroll
+                for (int off = LPN / 2; off >= 1; off >>= 1) dot += __shfl_xor_sync(FULL, dot, off);
+                const float e = sj[u] * dot;
+                if (sl == 0 && ok[u]) g.E[base + q + u * G + sub] = e;
+#pragma unroll
+                for (int v = 0; v < VPL; ++v)
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) acc[v][k] = fmaf(e, f[v][k], acc[v][k]);
+            }
+        }
+        c = c2;
+        s = s2;
+    }
+#pragma unroll
+    for (int off = LPN; off < 32; off <<= 1)
+#pragma unroll
+        for (int v = 0; v < VPL; ++v)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[v][k] += __shfl_xor_sync(FULL, acc[v][k], off);
+    if (lane < LPN) {
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+            if (!colok[v]) continue;
+            uint32_t w[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                __nv_bfloat162 h = __floats2bfloat162_rn(acc[v][2 * k], acc[v][2 * k + 1]);
+                w[k] = *reinterpret_cast<uint32_t *>(&h);
+            }
+            reinterpret_cast<uint4 *>(g.O + (int64_t)row * g.ldo)[v * LPN + sl] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) gnn_kernel(const GnnArgs a) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(a.ticket, 1u);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= (unsigned)a.ntiles) return;
+        const Tile tile = a.tiles[t];
+        const GraphDesc g = a.graphs[tile.graph];
+        for (int row = tile.row0; row < tile.row1; ++row) {
+            if (g.N <= 64)
+                gnn_row<8, 1, 4>(g, row, lane);
+            else if (g.N <= 128)
+                gnn_row<8, 2, 2>(g, row, lane);
+            else
+                gnn_row<16, 2, 2>(g, row, lane);
+        }
+    }
+}
+
+}  // namespace gnn
+}  // namespace gbsp
+
+using namespace gbsp;
+using namespace gbsp::gnn;
+
+struct gbsp_gnn_plan {
+    int device;
+    int G;
+    int ntiles;
+    int64_t nnz, rows;
+    GraphDesc *d_graphs;
+    Tile *d_tiles;
+    unsigned *d_ticket;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+namespace {
+
+void gnn_free(gbsp_gnn_plan *p) {
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    cudaFree(p->d_graphs);
+    cudaFree(p->d_tiles);
+    cudaFree(p->d_ticket);
+    delete p;
+}
+
+}  // namespace
+
+GBSP_EXPORT int gbsp_gnn_plan_create(int G, const gbsp_csr *S, const gbsp_dense *H, float *const *E,
+                                     gbsp_dense *O, int32_t edges_per_tile, void *stream, gbsp_gnn_plan **out) {
+    if (!out) return fail(GBSP_ERR_INVALID_ARG, "gnn plan: null output");
+    *out = nullptr;
+    if (G < 0 || (G > 0 && (!S || !H || !E || !O))) return fail(GBSP_ERR_INVALID_ARG, "gnn plan: bad arrays");
+    if (edges_per_tile <= 0) edges_per_tile = 2048;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<GraphDesc> graphs(G);
+    std::vector<Tile> tiles;
+    std::vector<int32_t> rp;
+    int64_t nnz = 0, rows = 0;
+    for (int g = 0; g < G; ++g) {
+        const gbsp_csr &a = S[g];
+        const gbsp_dense &h = H[g], &o = O[g];
+        if (a.rows != a.cols || a.rows < 0 || a.rows > 2147483647LL || a.nnz < 0 || a.dtype != GBSP_F32 ||
+            (a.rows > 0 && !a.rowptr) || (a.nnz > 0 && (!a.colidx || !a.vals || !E[g])))
+            return fail(GBSP_ERR_INVALID_ARG, "gnn plan: graph %d: S must be a square FP32 CSR with nnz given", g);
+        if (h.dtype != GBSP_BF16 || o.dtype != GBSP_BF16 || h.rows != a.rows || o.rows != a.rows ||
+            h.cols != o.cols || h.ld < h.cols || o.ld < o.cols)
+            return fail(GBSP_ERR_INVALID_ARG, "gnn plan: graph %d: H and O must be BF16 n x N", g);
+        if (h.cols % 8 || h.cols > 256 || h.ld % 8 || o.ld % 8 || !aligned16(h.data) || !aligned16(o.data))
+            return fail(GBSP_ERR_UNSUPPORTED, "gnn plan: graph %d: N must be a multiple of 8 up to 256 with "
+                        "16-byte aligned rows", g);
+        graphs[g] = GraphDesc{a.rowptr, a.colidx, static_cast<const float *>(a.vals),
+                              static_cast<const uint16_t *>(h.data), static_cast<uint16_t *>(o.data), E[g],
+                              h.ld, o.ld, (int32_t)a.rows, (int32_t)h.cols};
+        // tiles of consecutive rows holding about edges_per_tile edges
+        rp.resize((size_t)a.rows + 1);
+        if (a.rows > 0 &&
+            (cudaMemcpyAsync(rp.data(), a.rowptr, sizeof(int32_t) * rp.size(), cudaMemcpyDeviceToHost, s) !=
+                 cudaSuccess ||
+             cudaStreamSynchronize(s) != cudaSuccess))
+            return check_launch("gnn plan rowptr copy");
+        if (a.rows > 0 && (int64_t)rp[a.rows] != a.nnz)
+            return fail(GBSP_ERR_INVALID_CSR, "gnn plan: graph %d: rowptr[n] != nnz", g);
+        int32_t r0 = 0;
+        while (r0 < a.rows) {
+            int32_t r1 = r0 + 1;
+            while (r1 < a.rows && rp[r1 + 1] - rp[r0] <= edges_per_tile && r1 - r0 < 64) ++r1;
+            tiles.push_back(Tile{g, r0, r1});
+            r0 = r1;
+        }
+        nnz += a.nnz;
+        rows += a.rows;
+    }
+    gbsp_gnn_plan *p = new gbsp_gnn_plan();
+    cudaGetDevice(&p->device);
+    p->G = G;
+    p->ntiles = (int)tiles.size();
+    p->nnz = nnz;
+    p->rows = rows;
+    int st = GBSP_OK;
+    cudaStream_t cap = nullptr;
+    if (cudaMalloc(&p->d_graphs, sizeof(GraphDesc) * (size_t)(G > 0 ? G : 1)) != cudaSuccess ||
+        cudaMalloc(&p->d_tiles, sizeof(Tile) * (tiles.empty() ? 1 : tiles.size())) != cudaSuccess ||
+        cudaMalloc(&p->d_ticket, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        gnn_free(p);
+        return fail(GBSP_ERR_OOM, "gnn plan: allocation failed");
+    }
+    if ((G > 0 && cudaMemcpy(p->d_graphs, graphs.data(), sizeof(GraphDesc) * G, cudaMemcpyHostToDevice) !=
+                      cudaSuccess) ||
+        (!tiles.empty() &&
+         cudaMemcpy(p->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice) != cudaSuccess)) {
+        st = check_launch("gnn plan upload");
+        gnn_free(p);
+        return st ? st : fail(GBSP_ERR_CUDA, "gnn plan upload");
+    }
+    // record: ticket reset + one persistent launch
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gnn_kernel, 256, 0);
+    const int nblocks = sm_count() * (per_sm < 1 ? 1 : per_sm);
+    GnnArgs args{p->d_graphs, p->d_tiles, p->ntiles, p->d_ticket};
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+        st = check_launch("gnn plan stream");
+        gnn_free(p);
+        return st ? st : fail(GBSP_ERR_CUDA, "gnn plan stream");
+    }
+    bool okc = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (okc) {
+        cudaMemsetAsync(p->d_ticket, 0, sizeof(unsigned), cap);
+        if (p->ntiles > 0) gnn_kernel<<<nblocks, 256, 0, cap>>>(args);
+        okc = cudaStreamEndCapture(cap, &p->graph) == cudaSuccess;
+    }
+    okc = okc && cudaGraphInstantiate(&p->exec, p->graph, 0) == cudaSuccess;
+    cudaStreamDestroy(cap);
+    if (!okc) {
+        st = check_launch("gnn plan capture");
+        gnn_free(p);
+        return st ? st : fail(GBSP_ERR_CUDA, "gnn plan: graph capture failed");
+    }
+    *out = p;
+    return ok();
+}
+
+GBSP_EXPORT int gbsp_gnn_plan_execute(const gbsp_gnn_plan *p, void *stream) {
+    if (!p) return fail(GBSP_ERR_INVALID_ARG, "gnn execute: null plan");
+    if (cudaGraphLaunch(p->exec, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return check_launch("gnn execute");
+    if (p->ntiles > 0) count_launches(1);
+    return ok();
+}
+
+GBSP_EXPORT int gbsp_gnn_plan_info(const gbsp_gnn_plan *p, int64_t *info, int n) {
+    if (!p || !info || n < 4) return fail(GBSP_ERR_INVALID_ARG, "gnn info: need room for 4 values");
+    info[0] = p->G;
+    info[1] = p->ntiles;
+    info[2] = p->rows;
+    info[3] = p->nnz;
+    return ok();
+}
+
+GBSP_EXPORT void gbsp_gnn_plan_destroy(gbsp_gnn_plan *p) { gnn_free(p); }
+
+GBSP_EXPORT int gnn_sddmm_spmm_batched(int G, const gbsp_csr *S, const gbsp_dense *H, float *const *E,
+                                       gbsp_dense *O, void *stream) {
+    gbsp_gnn_plan *p = nullptr;
+    int st = gbsp_gnn_plan_create(G, S, H, E, O, 0, stream, &p);
+    if (st) return st;
+    st = gbsp_gnn_plan_execute(p, stream);
+    if (!st && cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        st = check_launch("gnn batched");
+    gnn_free(p);
+    return st ? st : ok();
+}

@@ -24,14 +24,58 @@ __device__ __forceinline__ float coef(const SpmmProblem &P, int64_t p, int c) {
     return a;
 }
 
-template <class EL, int LPN, int VPL, int U>
+// One step of a group: U nonzeros per group (G * U per warp), VPL 16-byte vectors per lane
+// each.  CHECK_NNZ guards a partial chunk (entries past cnt are skipped), CHECK_COLS a
+// partial column tile (vectors past N are skipped); the full-chunk, full-tile case issues
+// its loads unpredicated.
+template <class EL, int LPN, int VPL, int U, bool CHECK_COLS, bool CHECK_NNZ>
+__device__ __forceinline__ void gather_step(const uint4 *__restrict__ Bv, int64_t ldv, int c, float a, int q,
+                                            int cnt, int sub, const bool (&colok)[VPL],
+                                            float (&acc)[VPL][EL::V]) {
+    constexpr int G = 32 / LPN;
+    uint4 raw[U][VPL];
+    float aj[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int idx = q + u * G + sub;
+        const int cj = __shfl_sync(FULL, c, idx);
+        aj[u] = __shfl_sync(FULL, a, idx);
+        const uint4 *rp = Bv + (int64_t)cj * ldv;
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+            if constexpr (CHECK_COLS || CHECK_NNZ) {
+                bool ok = true;
+                if constexpr (CHECK_NNZ) ok = idx < cnt;
+                if constexpr (CHECK_COLS) ok = ok && colok[v];
+                raw[u][v] = ok ? ld_gather16(rp + v * LPN) : make_uint4(0, 0, 0, 0);
+            } else {
+                raw[u][v] = ld_gather16(rp + v * LPN);
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+            float f[EL::V];
+            EL::unpack(raw[u][v], f);
+#pragma unroll
+            for (int k = 0; k < EL::V; ++k) acc[v][k] = fmaf(aj[u], f[k], acc[v][k]);
+        }
+    }
+}
+
+// Accumulates the stored entries [p0, p1) of one row into acc (the lane's VPL vectors of
+// the row's column tile starting at col_base).
+template <class EL, int LPN, int VPL, int U, bool CHECK_COLS>
 __device__ __forceinline__ void gather_range(const SpmmProblem &P, int64_t p0, int64_t p1,
                                              float (&acc)[VPL][EL::V], int lane, int col_base) {
     constexpr int G = 32 / LPN;
-    static_assert(G * U <= 32, "a chunk of 32 nonzeros must hold whole steps");
+    constexpr int STEP = G * U;
+    static_assert(STEP <= 32 && 32 % STEP == 0, "a chunk of 32 nonzeros must hold whole steps");
     const int sub = lane / LPN;
-    const char *B = static_cast<const char *>(P.B);
-    const int64_t ldb_bytes = P.ldb * (int64_t)sizeof(typename EL::stored);
+    const uint4 *Bv = static_cast<const uint4 *>(P.B) + col_base / EL::V;
+    const int64_t ldv = P.ldb / EL::V;
     bool colok[VPL];
 #pragma unroll
     for (int v = 0; v < VPL; ++v) colok[v] = col_base + v * LPN * EL::V < P.N;
@@ -51,36 +95,15 @@ __device__ __forceinline__ void gather_range(const SpmmProblem &P, int64_t p0, i
             c2 = ld_stream(P.colidx + nb + lane);
             a2 = coef<EL>(P, nb + lane, c2);
         }
-        const int cnt = (int)min((int64_t)32, p1 - base);
+        if (nb <= p1) {
+#pragma unroll
+            for (int q = 0; q < 32; q += STEP)
+                gather_step<EL, LPN, VPL, U, CHECK_COLS, false>(Bv, ldv, c, a, q, 32, sub, colok, acc);
+        } else {
+            const int cnt = (int)(p1 - base);
 #pragma unroll 1
-        for (int q = 0; q < cnt; q += G * U) {
-            float aj[U];
-            uint4 raw[U][VPL];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int idx = q + u * G + sub;
-                const int cj = __shfl_sync(FULL, c, idx);
-                aj[u] = __shfl_sync(FULL, a, idx);
-                const bool ok = idx < cnt;
-                const char *row = B + (int64_t)cj * ldb_bytes;
-#pragma unroll
-                for (int v = 0; v < VPL; ++v) {
-                    raw[u][v] = make_uint4(0, 0, 0, 0);
-                    if (ok && colok[v])
-                        raw[u][v] = ld_gather16(row + (int64_t)(col_base + v * LPN * EL::V) *
-                                                          (int64_t)sizeof(typename EL::stored));
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-#pragma unroll
-                for (int v = 0; v < VPL; ++v) {
-                    float f[EL::V];
-                    EL::unpack(raw[u][v], f);
-#pragma unroll
-                    for (int k = 0; k < EL::V; ++k) acc[v][k] = fmaf(aj[u], f[k], acc[v][k]);
-                }
-            }
+            for (int q = 0; q < cnt; q += STEP)
+                gather_step<EL, LPN, VPL, U, CHECK_COLS, true>(Bv, ldv, c, a, q, cnt, sub, colok, acc);
         }
         base = nb;
         c = c2;
@@ -133,31 +156,13 @@ __global__ void __launch_bounds__(256) spmm_rowsplit_kernel(const SpmmProblem P)
     for (int v = 0; v < VPL; ++v)
 #pragma unroll
         for (int k = 0; k < EL::V; ++k) acc[v][k] = 0.f;
-    gather_range<EL, LPN, VPL, U>(P, __ldg(P.rowptr + row), __ldg(P.rowptr + row + 1), acc, lane, col_base);
+    const int64_t p0 = __ldg(P.rowptr + row), p1 = __ldg(P.rowptr + row + 1);
+    if ((blockIdx.y + 1) * (LPN * VPL * EL::V) <= P.N)
+        gather_range<EL, LPN, VPL, U, false>(P, p0, p1, acc, lane, col_base);
+    else
+        gather_range<EL, LPN, VPL, U, true>(P, p0, p1, acc, lane, col_base);
     reduce_groups<EL, LPN, VPL>(acc);
     store_row<EL, LPN, VPL>(P.C + (int64_t)row * P.ldc, acc, lane, col_base, P.N, row_scale<EL>(P, row));
-}
-
-// Merge-path coordinate of diagonal d over the two lists "row ends" (rowptr[1..M]) and
-// "stored entries" (0..nnz-1): the number x of rows fully consumed, with y = d - x
-// entries consumed.  Row end i precedes entry j exactly when rowptr[i + 1] <= j.
-// The warp evaluates 32 probes per round (a 33-ary search), then settles the last <= 32.
-__device__ __forceinline__ int merge_search(const int32_t *rowptr, int M, int64_t nnz, int64_t d, int lane) {
-    int64_t lo = d - nnz > 0 ? d - nnz : 0;
-    int64_t hi = d < M ? d : M;
-    while (hi - lo > 32) {
-        const int64_t span = hi - lo;
-        const int64_t probe = lo + (span * (lane + 1)) / 33;
-        const bool t = (int64_t)__ldg(rowptr + probe + 1) + probe + 1 <= d;
-        const int k = __popc(__ballot_sync(FULL, t));
-        const int64_t new_lo = k == 0 ? lo : lo + (span * k) / 33 + 1;
-        const int64_t new_hi = k == 32 ? hi : lo + (span * (k + 1)) / 33;
-        lo = new_lo;
-        hi = new_hi;
-    }
-    const int64_t x = lo + lane;
-    const bool t = x < hi && (int64_t)__ldg(rowptr + x + 1) + x + 1 <= d;
-    return (int)(lo + __popc(__ballot_sync(FULL, t)));
 }
 
 // nnz-balanced split: warp w takes the items [w * ipw, (w + 1) * ipw) of the merge path
@@ -186,9 +191,13 @@ __global__ void __launch_bounds__(256) spmm_merge_kernel(const SpmmProblem P, in
     for (int v = 0; v < VPL; ++v)
 #pragma unroll
         for (int k = 0; k < EL::V; ++k) acc[v][k] = 0.f;
+    const bool full_tile = (blockIdx.y + 1) * TW <= P.N;
     for (int row = x0; row < x1; ++row) {
         const int64_t e = __ldg(P.rowptr + row + 1);
-        gather_range<EL, LPN, VPL, U>(P, p, e, acc, lane, col_base);
+        if (full_tile)
+            gather_range<EL, LPN, VPL, U, false>(P, p, e, acc, lane, col_base);
+        else
+            gather_range<EL, LPN, VPL, U, true>(P, p, e, acc, lane, col_base);
         reduce_groups<EL, LPN, VPL>(acc);
         store_row<EL, LPN, VPL>(P.C + (int64_t)row * P.ldc, acc, lane, col_base, P.N, row_scale<EL>(P, row));
 #pragma unroll
@@ -197,7 +206,10 @@ __global__ void __launch_bounds__(256) spmm_merge_kernel(const SpmmProblem P, in
             for (int k = 0; k < EL::V; ++k) acc[v][k] = 0.f;
         p = e;
     }
-    gather_range<EL, LPN, VPL, U>(P, p, y1, acc, lane, col_base);
+    if (full_tile)
+        gather_range<EL, LPN, VPL, U, false>(P, p, y1, acc, lane, col_base);
+    else
+        gather_range<EL, LPN, VPL, U, true>(P, p, y1, acc, lane, col_base);
     reduce_groups<EL, LPN, VPL>(acc);
     float *cv = carry_val + ((int64_t)blockIdx.y * nwarps + w) * TW;
     if (lane < LPN) {

@@ -1,4 +1,5 @@
-// Host-side choice of lane layout and launch shape for the SpMM kernels of one element type.
+// Host-side choice of lane layout and launch shape for the SpMM kernels: one translation
+// unit per (element type, algorithm) instantiates launch_spmm_algo.
 #pragma once
 
 #include "spmm_kernels.cuh"
@@ -6,11 +7,11 @@
 namespace gbsp {
 namespace spmm_detail {
 
-template <class EL, int LPN, int VPL, int U>
-int run(const SpmmProblem &P, int variant, int ctas_per_sm, cudaStream_t s) {
+template <class EL, int LPN, int VPL, int U, int ALGO>
+int run(const SpmmProblem &P, int ctas_per_sm, cudaStream_t s) {
     constexpr int TW = LPN * VPL * EL::V;
     const int ntiles = (P.N + TW - 1) / TW;
-    if (variant == GBSP_VARIANT_MERGE) {
+    if constexpr (ALGO == GBSP_VARIANT_MERGE) {
         int per_sm = ctas_per_sm;
         if (per_sm <= 0) {
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spmm_merge_kernel<EL, LPN, VPL, U>, 256, 0) !=
@@ -37,48 +38,77 @@ int run(const SpmmProblem &P, int variant, int ctas_per_sm, cudaStream_t s) {
         scratch_free(cv, s);
         scratch_free(cr, s);
         return st;
+    } else {
+        spmm_rowsplit_kernel<EL, LPN, VPL, U><<<dim3((P.M + 7) / 8, ntiles), 256, 0, s>>>(P);
+        count_launches(1);
+        return check_launch("spmm rowsplit");
     }
-    spmm_rowsplit_kernel<EL, LPN, VPL, U><<<dim3((P.M + 7) / 8, ntiles), 256, 0, s>>>(P);
-    count_launches(1);
-    return check_launch("spmm rowsplit");
 }
 
-template <class EL, int LPN, int VPL>
-int by_unroll(const SpmmProblem &P, int variant, int u, int cps, cudaStream_t s) {
-    if constexpr (LPN >= 8) {
-        if (u >= 8) return run<EL, LPN, VPL, 8>(P, variant, cps, s);
+// Gathers in flight per lane: U <= LPN keeps a step inside one chunk of 32 nonzeros,
+// VPL * U <= 16 bounds the registers holding loads in flight.
+template <class EL, int LPN, int VPL, int ALGO>
+int by_unroll(const SpmmProblem &P, int u, int cps, cudaStream_t s) {
+    constexpr int UMAX = LPN < 16 / VPL ? LPN : 16 / VPL;
+    if constexpr (UMAX >= 8) {
+        if (u >= 8) return run<EL, LPN, VPL, 8, ALGO>(P, cps, s);
     }
-    if constexpr (LPN >= 4) {
-        if (u >= 4) return run<EL, LPN, VPL, 4>(P, variant, cps, s);
+    if constexpr (UMAX >= 4) {
+        if (u >= 4) return run<EL, LPN, VPL, 4, ALGO>(P, cps, s);
     }
-    if constexpr (LPN >= 2) {
-        return run<EL, LPN, VPL, 2>(P, variant, cps, s);
+    if constexpr (UMAX >= 2) {
+        return run<EL, LPN, VPL, 2, ALGO>(P, cps, s);
     } else {
-        return run<EL, LPN, VPL, 1>(P, variant, cps, s);
+        return run<EL, LPN, VPL, 1, ALGO>(P, cps, s);
     }
+}
+
+template <class EL, int VPL, int ALGO>
+int by_lanes(const SpmmProblem &P, int lpn, int u, int cps, cudaStream_t s) {
+    if constexpr (VPL * EL::V > 16) {  // at most 16 accumulators per lane
+        return fail(GBSP_ERR_UNSUPPORTED, "spmm: %d vectors per lane exceed 16 elements", VPL);
+    } else switch (lpn) {
+        case 1: if constexpr (VPL == 1) return by_unroll<EL, 1, 1, ALGO>(P, u, cps, s); break;
+        case 2: if constexpr (VPL == 1) return by_unroll<EL, 2, 1, ALGO>(P, u, cps, s); break;
+        case 4: if constexpr (VPL <= 2) return by_unroll<EL, 4, VPL, ALGO>(P, u, cps, s); break;
+        case 8: return by_unroll<EL, 8, VPL, ALGO>(P, u, cps, s);
+        case 16: return by_unroll<EL, 16, VPL, ALGO>(P, u, cps, s);
+        case 32: return by_unroll<EL, 32, VPL, ALGO>(P, u, cps, s);
+    }
+    return fail(GBSP_ERR_UNSUPPORTED, "spmm: no kernel for %d lanes x %d vectors", lpn, VPL);
 }
 
 }  // namespace spmm_detail
 
-template <class EL>
-int launch_spmm_typed(const SpmmProblem &P, int variant, int unroll, int ctas_per_sm, cudaStream_t s) {
+// Lane layout: VPL vectors per lane (default 2 once a row spans 16 vectors, else 1, so a
+// row keeps at least 8 lanes and every load instruction covers whole 128-byte lines; at
+// most 16 / V so a lane holds at most 16 accumulators) and LPN = the power of two covering
+// the row's vectors, at most 32 (wider rows take several column tiles).  Layouts with
+// VPL > 1 need at least 4 (VPL = 2) or 8 (VPL = 4) lanes.
+inline void spmm_layout(int nvec, int vecs, int max_vpl, int &lpn, int &vpl) {
+    vpl = vecs > 0 ? vecs : (nvec >= 16 ? 2 : 1);
+    if (vpl > max_vpl) vpl = max_vpl;
+    lpn = next_pow2((nvec + vpl - 1) / vpl);
+    if (lpn > 32) lpn = 32;
+    while ((vpl == 4 && lpn < 8) || (vpl == 2 && lpn < 4)) {
+        vpl >>= 1;
+        lpn = next_pow2((nvec + vpl - 1) / vpl);
+        if (lpn > 32) lpn = 32;
+    }
+}
+
+template <class EL, int ALGO>
+int launch_spmm_algo(const SpmmProblem &P, int vecs, int unroll, int ctas_per_sm, cudaStream_t s) {
     using namespace spmm_detail;
-    if (variant == GBSP_VARIANT_SCALAR) {
-        spmm_scalar_kernel<EL><<<dim3((P.M + 7) / 8, 1), 256, 0, s>>>(P);
-        count_launches(1);
-        return check_launch("spmm scalar");
+    int lpn, vpl;
+    spmm_layout(P.N / EL::V, vecs, 16 / EL::V, lpn, vpl);  // N % V == 0 is checked by the caller
+    const int u = unroll > 0 ? unroll : (vpl == 1 ? 8 : 4);
+    switch (vpl) {
+        case 1: return by_lanes<EL, 1, ALGO>(P, lpn, u, ctas_per_sm, s);
+        case 2: return by_lanes<EL, 2, ALGO>(P, lpn, u, ctas_per_sm, s);
+        case 4: return by_lanes<EL, 4, ALGO>(P, lpn, u, ctas_per_sm, s);
     }
-    const int nvec = P.N / EL::V;  // N % V == 0 is checked by the caller
-    const int u = unroll > 0 ? unroll : 4;
-    if (nvec > 32) return by_unroll<EL, 32, 2>(P, variant, u, ctas_per_sm, s);
-    switch (next_pow2(nvec)) {
-        case 1: return by_unroll<EL, 1, 1>(P, variant, u, ctas_per_sm, s);
-        case 2: return by_unroll<EL, 2, 1>(P, variant, u, ctas_per_sm, s);
-        case 4: return by_unroll<EL, 4, 1>(P, variant, u, ctas_per_sm, s);
-        case 8: return by_unroll<EL, 8, 1>(P, variant, u, ctas_per_sm, s);
-        case 16: return by_unroll<EL, 16, 1>(P, variant, u, ctas_per_sm, s);
-        default: return by_unroll<EL, 32, 1>(P, variant, u, ctas_per_sm, s);
-    }
+    return fail(GBSP_ERR_INVALID_ARG, "spmm: vectors per lane must be 1, 2 or 4");
 }
 
 }  // namespace gbsp

@@ -1,0 +1,677 @@
+// Condensed-tile tensor-core SpMM: the dense 16 x 8 blocks of A run on tcgen05, the rest of
+// A on the CSR kernels.
+//
+// Plan (once per sparsity pattern): A is cut into windows of 16 rows and each window into
+// aligned 16 x 8 blocks; a block holding at least `threshold` stored entries is dense.  A
+// window's dense blocks, in column order and padded to a multiple of 8, form a condensed
+// 16 x Kc tile of A (Kc = 8 * blocks) stored as BF16 in the shared-memory image that the
+// MMA reads (K-major, 128-byte swizzle), 16 x 64 per stage.  The remaining entries form a
+// residual CSR matrix.
+//
+// Execute: the residual SpMM writes C; then one CTA per window with dense blocks computes
+//   C_w^T (N x 16) = B_g^T (N x Kc) * A_w^T (Kc x 16)
+// with tcgen05.mma kind::f16 (BF16 in, FP32 accumulate in TMEM): the feature dimension
+// is the MMA's M (128 per tile, up to 4 tiles), the 16 window rows its N, the condensed
+// columns its K.  B_g, the B rows of the dense blocks, is gathered by TMA straight into
+// the MMA's MN-major layout (8 rows x 64 features per 1 KB swizzled atom; rows past K are
+// zero-filled, which also serves the padding blocks).  The epilogue reads TMEM and adds the
+// window's 16 rows into C.
+#include <cuda.h>
+
+#include <mutex>
+
+#include "common.cuh"
+
+namespace gbsp {
+
+int device_exclusive_scan(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
+
+namespace tc {
+
+constexpr int kBR = 16;        // rows of a dense block (= rows of a window)
+constexpr int kBC = 8;         // columns of a dense block
+constexpr int kKCH = 64;       // condensed columns per pipeline stage
+constexpr int kBlkPerCh = kKCH / kBC;
+constexpr int kATile = kBR * kKCH * 2;  // bytes of one stage of window values
+constexpr uint64_t kWaitNs = 1000000000ull;  // a bounded wait gives up after one second
+
+// ---- PTX wrappers ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase with the given parity to complete; false after about a second.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > kWaitNs) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// 32 TMEM lanes (one per thread of the warp) x 16 consecutive 32-bit columns.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor (128-byte swizzle): start address, leading and stride
+// byte offsets (all >> 4), descriptor version 1, swizzle mode 2 in bits 61-63.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, A MN-major
+// (feature-contiguous B rows), B K-major (condensed window rows), M = 128, N = 16.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+struct TcArgs {
+    const int32_t *win_row0;  // first row of each window that has dense blocks
+    const int32_t *win_blk;   // [nwin + 1] offsets of each window's (padded) dense blocks
+    const int32_t *blk_col;   // block-column index of each dense block, -1 for padding
+    const uint8_t *atiles;    // 2 KB swizzled value tiles, one per 8 dense blocks
+    float *C;
+    int64_t ldc;
+    int M, K, N;
+    int *err;  // set on a timed-out wait
+};
+
+template <int NT>
+struct TcShape {
+    static constexpr int NFA = 2 * NT;                      // 64-feature atoms per k-row group
+    static constexpr int BT = kKCH * NT * 128 * 2;          // gathered B bytes per stage
+    static constexpr int STAGE = BT + kATile;               // bytes per stage
+    static constexpr int S = NT <= 2 ? 4 : (NT == 3 ? 3 : 2);  // pipeline depth
+    static constexpr int NCOLS = NT <= 2 ? 32 : 64;         // TMEM columns (16 per feature tile)
+    static constexpr int SMEM = S * STAGE + 1024 + 256;     // + alignment slack + barriers
+};
+
+template <int NT>
+__global__ void __launch_bounds__(128, 1) tc_window_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
+    using SH = TcShape<NT>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + SH::S * SH::STAGE);
+    uint64_t *empty = full + SH::S;
+    uint64_t *done = empty + SH::S;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w = blockIdx.x;
+    const int b0 = a.win_blk[w], b1 = a.win_blk[w + 1];
+    const int nch = (b1 - b0) / kBlkPerCh;
+    const int row0 = a.win_row0[w];
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < SH::S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+    }
+    if (warp == 0) tmem_alloc(tslot, SH::NCOLS);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t taddr = *tslot;
+
+    if (threadIdx.x == 0) {
+        auto issue = [&](int s, int ch) {
+            uint8_t *bt = smem + s * SH::STAGE;
+            mbar_expect_tx(&full[s], SH::STAGE);
+            bulk_load(bt + SH::BT, a.atiles + (size_t)(b0 / kBlkPerCh + ch) * kATile, kATile, &full[s]);
+#pragma unroll 1
+            for (int kb = 0; kb < kBlkPerCh; ++kb) {
+                const int col = a.blk_col[b0 + ch * kBlkPerCh + kb];
+                const int y = col >= 0 ? col * kBC : a.K;  // padding block: rows past K read as zeros
+#pragma unroll
+                for (int fa = 0; fa < SH::NFA; ++fa) tma_load_2d(bt + (kb * SH::NFA + fa) * 1024, &tmB, &full[s], 64 * fa, y);
+            }
+        };
+        bool ok = true;
+        const int pro = nch < SH::S ? nch : SH::S;
+        for (int s = 0; s < pro; ++s) issue(s, s);
+        int issued = pro, consumed = 0;
+        for (int i = 0; i < nch; ++i) {
+            const int s = i % SH::S;
+            if (!mbar_wait(&full[s], (i / SH::S) & 1)) {
+                ok = false;
+                break;
+            }
+            consumed = i + 1;
+            fence_after_sync();
+            const uint32_t bt = smem_u32(smem + s * SH::STAGE);
+            const uint32_t at = bt + SH::BT;
+#pragma unroll
+            for (int j = 0; j < kKCH / 16; ++j) {
+                const uint64_t bdesc = smem_desc(at + j * 32, 16, 1024);
+#pragma unroll
+                for (int h = 0; h < NT; ++h) {
+                    const uint64_t adesc = smem_desc(bt + ((2 * j) * SH::NFA + 2 * h) * 1024, 1024, SH::NFA * 1024);
+                    mma_bf16(taddr + h * 16, adesc, bdesc, kIdesc, (i > 0 || j > 0) ? 1u : 0u);
+                }
+            }
+            mma_commit(&empty[s]);
+            // refill the stage of the previous chunk once its MMAs have finished
+            if (i >= 1 && i - 1 + SH::S < nch) {
+                const int sp = (i - 1) % SH::S;
+                if (!mbar_wait(&empty[sp], ((i - 1) / SH::S) & 1)) {
+                    ok = false;
+                    break;
+                }
+                issue(sp, i - 1 + SH::S);
+                ++issued;
+            }
+        }
+        mma_commit(done);
+        if (!ok) {
+            atomicExch(a.err, 1);
+            // let the copies already issued land (each wait is bounded) before the CTA exits
+            for (int i = consumed; i < issued; ++i) mbar_wait(&full[i % SH::S], (i / SH::S) & 1);
+        }
+    }
+    __syncwarp();
+    const bool have = mbar_wait(done, 0);
+    fence_after_sync();
+    if (!have) {
+        if (lane == 0) atomicExch(a.err, 2);
+    } else {
+#pragma unroll
+        for (int h = 0; h < NT; ++h) {
+            float v[16];
+            tmem_ld16(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)(h * 16), v);
+            const int f = 128 * h + 32 * warp + lane;
+            if (f < a.N) {
+#pragma unroll
+                for (int r = 0; r < kBR; ++r) {
+                    const int row = row0 + r;
+                    if (row < a.M) a.C[(int64_t)row * a.ldc + f] += v[r];
+                }
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(taddr, SH::NCOLS);
+}
+
+// ---- plan kernels ---------------------------------------------------------------------------
+
+// cnt[w * nbc + bc] += 1 for each stored entry of window w in block column bc; also flags
+// rows whose column indices are not strictly increasing.
+__global__ void count_blocks_kernel(const int32_t *rowptr, const int32_t *colidx, int M, int nbc, int32_t *cnt,
+                                    int *unsorted) {
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= M) return;
+    const int64_t p0 = rowptr[row], p1 = rowptr[row + 1];
+    int32_t *c = cnt + (int64_t)(row / kBR) * nbc;
+    for (int64_t p = p0 + lane; p < p1; p += 32) {
+        const int col = colidx[p];
+        atomicAdd(c + col / kBC, 1);
+        if (p > p0 && colidx[p - 1] >= col) atomicExch(unsorted, 1);
+    }
+}
+
+// Per window: block columns with at least `threshold` entries become dense blocks, numbered
+// in column order (cnt is overwritten with the slot number, or -1).
+__global__ void __launch_bounds__(256) mark_dense_kernel(int32_t *cnt, int nbc, int threshold, int32_t *win_nb) {
+    __shared__ int32_t warp_tot[8];
+    __shared__ int32_t carry;
+    const int w = blockIdx.x;
+    int32_t *c = cnt + (int64_t)w * nbc;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b = 0; b < nbc; b += 256) {
+        const int bc = b + threadIdx.x;
+        const int dense = (bc < nbc && c[bc] >= threshold) ? 1 : 0;
+        const unsigned bal = __ballot_sync(FULL, dense);
+        const int before_in_warp = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) warp_tot[warp] = __popc(bal);
+        __syncthreads();
+        int before = carry;
+        for (int q = 0; q < warp; ++q) before += warp_tot[q];
+        if (bc < nbc) c[bc] = dense ? before + before_in_warp : -1;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int q = 0; q < 8; ++q) t += warp_tot[q];
+            carry += t;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) win_nb[w] = carry;
+}
+
+__global__ void pad_counts_kernel(const int32_t *win_nb, int nwin, int32_t *padded, int32_t *has) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nwin) return;
+    const int n = win_nb[w];
+    padded[w] = (n + kBlkPerCh - 1) / kBlkPerCh * kBlkPerCh;
+    has[w] = n > 0 ? 1 : 0;
+}
+
+// Block columns of each window's dense blocks, padding slots, and the compact window list.
+__global__ void __launch_bounds__(256) fill_blocks_kernel(const int32_t *slot, int nbc, const int32_t *win_off,
+                                                          const int32_t *win_nb, const int32_t *tc_index,
+                                                          int32_t *blk_col, int32_t *tc_row0, int32_t *tc_blk) {
+    const int w = blockIdx.x;
+    const int nb = win_nb[w];
+    if (nb == 0) return;
+    const int off = win_off[w];
+    const int npad = win_off[w + 1] - off;
+    const int32_t *s = slot + (int64_t)w * nbc;
+    for (int bc = threadIdx.x; bc < nbc; bc += blockDim.x)
+        if (s[bc] >= 0) blk_col[off + s[bc]] = bc;
+    for (int q = nb + threadIdx.x; q < npad; q += blockDim.x) blk_col[off + q] = -1;
+    if (threadIdx.x == 0) {
+        const int t = tc_index[w];
+        tc_row0[t] = w * kBR;
+        tc_blk[t] = off;
+        tc_blk[t + 1] = off + npad;  // the next window writes the same value as its start
+    }
+}
+
+// Byte offset of element (r, k) of a 16 x 64 BF16 tile in the K-major 128-byte-swizzled
+// image: 8-row atoms of 1 KB, 128 B per row, 16-byte chunks XOR-ed with the row in the atom.
+__device__ __forceinline__ int atile_offset(int r, int k) {
+    const int chunk = (k * 2) >> 4;
+    return (r >> 3) * 1024 + (r & 7) * 128 + ((chunk ^ (r & 7)) << 4) + ((k * 2) & 15);
+}
+
+// Scatters the entries of dense blocks into the value tiles and counts the rest per row.
+__global__ void fill_values_kernel(const int32_t *rowptr, const int32_t *colidx, const uint16_t *vals, int M,
+                                   int nbc, const int32_t *slot, const int32_t *win_off, uint8_t *atiles,
+                                   int32_t *res_len) {
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= M) return;
+    const int w = row / kBR, r = row % kBR;
+    const int32_t *s = slot + (int64_t)w * nbc;
+    const int off = win_off[w];
+    const int64_t p0 = rowptr[row], p1 = rowptr[row + 1];
+    int resid = 0;
+    for (int64_t p = p0 + lane; p < p1; p += 32) {
+        const int col = colidx[p];
+        const int sl = s[col / kBC];
+        if (sl >= 0) {
+            const int blk = off + sl;
+            const int k = (blk % kBlkPerCh) * kBC + col % kBC;
+            uint8_t *tile = atiles + (int64_t)(blk / kBlkPerCh) * kATile;
+            *reinterpret_cast<uint16_t *>(tile + atile_offset(r, k)) = vals[p];
+        } else {
+            ++resid;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) resid += __shfl_xor_sync(FULL, resid, o);
+    if (lane == 0) res_len[row] = resid;
+}
+
+// Copies the residual entries of each row, in order, to the residual CSR.
+__global__ void fill_residual_kernel(const int32_t *rowptr, const int32_t *colidx, const uint16_t *vals, int M,
+                                     int nbc, const int32_t *slot, const int32_t *res_ptr, int32_t *res_col,
+                                     uint16_t *res_val) {
+    const int lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= M) return;
+    const int32_t *s = slot + (int64_t)(row / kBR) * nbc;
+    const int64_t p0 = rowptr[row], p1 = rowptr[row + 1];
+    int64_t out = res_ptr[row];
+    for (int64_t base = p0; base < p1; base += 32) {
+        const int64_t p = base + lane;
+        int col = 0;
+        bool keep = false;
+        if (p < p1) {
+            col = colidx[p];
+            keep = s[col / kBC] < 0;
+        }
+        const unsigned bal = __ballot_sync(FULL, keep);
+        if (keep) {
+            const int64_t q = out + __popc(bal & ((1u << lane) - 1u));
+            res_col[q] = col;
+            res_val[q] = vals[p];
+        }
+        out += __popc(bal);
+    }
+}
+
+}  // namespace tc
+}  // namespace gbsp
+
+// ---- plan object and entry points -----------------------------------------------------------
+
+using namespace gbsp;
+using namespace gbsp::tc;
+
+struct gbsp_plan {
+    int device;
+    int64_t M, K, nnz;
+    int threshold;
+    int nwin_tc;         // windows with dense blocks
+    int64_t nblocks;     // dense blocks, padded per window to a multiple of 8
+    int64_t dense_nnz;   // stored entries inside dense blocks
+    int64_t res_nnz;     // residual entries
+    int32_t *tc_row0, *tc_blk, *blk_col;
+    uint8_t *atiles;
+    int32_t *res_rowptr, *res_colidx;
+    uint16_t *res_vals;
+    int *err;
+    gbsp_opts residual_opts;
+};
+
+namespace {
+
+template <class T>
+int dev_alloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GBSP_ERR_OOM, "plan: allocation of %zu bytes failed", count * sizeof(T));
+    }
+    return GBSP_OK;
+}
+
+void plan_free(gbsp_plan *p) {
+    if (!p) return;
+    cudaFree(p->tc_row0);
+    cudaFree(p->tc_blk);
+    cudaFree(p->blk_col);
+    cudaFree(p->atiles);
+    cudaFree(p->res_rowptr);
+    cudaFree(p->res_colidx);
+    cudaFree(p->res_vals);
+    cudaFree(p->err);
+    delete p;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+template <int NT>
+int launch_tc(const CUtensorMap &map, const TcArgs &args, int nwin, cudaStream_t s) {
+    using SH = TcShape<NT>;
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (!attr_set[dev]) {
+        if (cudaFuncSetAttribute(tc_window_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM) !=
+            cudaSuccess)
+            return check_launch("tc smem attribute");
+        attr_set[dev] = true;
+    }
+    tc_window_kernel<NT><<<nwin, 128, SH::SMEM, s>>>(map, args);
+    count_launches(1);
+    return check_launch("tc window kernel");
+}
+
+}  // namespace
+
+GBSP_EXPORT int gbsp_plan_create(const gbsp_csr *A, int32_t threshold, const gbsp_opts *residual_opts, void *stream,
+                                 gbsp_plan **out) {
+    if (!out) return fail(GBSP_ERR_INVALID_ARG, "plan: null output");
+    *out = nullptr;
+    if (!A || A->rows < 0 || A->cols < 0 || A->nnz < 0 || A->rows > 2147483647LL || A->cols > 2147483647LL)
+        return fail(GBSP_ERR_INVALID_ARG, "plan: bad CSR descriptor");
+    if (A->dtype != GBSP_BF16) return fail(GBSP_ERR_UNSUPPORTED, "plan: the tensor-core path takes BF16 values");
+    if (A->rows > 0 && !A->rowptr) return fail(GBSP_ERR_INVALID_ARG, "plan: null rowptr");
+    if (A->nnz > 0 && (!A->colidx || !A->vals)) return fail(GBSP_ERR_INVALID_ARG, "plan: null colidx / vals");
+    if (threshold < 1) threshold = 16;
+    const int64_t M = A->rows, K = A->cols;
+    const int64_t nwin = (M + kBR - 1) / kBR, nbc = (K + kBC - 1) / kBC;
+    if (nwin * nbc > (int64_t)1 << 28)
+        return fail(GBSP_ERR_UNSUPPORTED, "plan: %lld windows x %lld block columns exceed the block map",
+                    (long long)nwin, (long long)nbc);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    gbsp_plan *p = new gbsp_plan();
+    cudaGetDevice(&p->device);
+    p->M = M;
+    p->K = K;
+    p->nnz = A->nnz;
+    p->threshold = threshold;
+    p->residual_opts = residual_opts ? *residual_opts : gbsp_opts{};
+    int st = GBSP_OK;
+    int32_t *slot = nullptr, *win_nb = nullptr, *padded = nullptr, *has = nullptr, *win_off = nullptr,
+            *tc_index = nullptr, *res_len = nullptr;
+    int *flag = nullptr;
+    int32_t totals[2] = {0, 0};
+    int hflag = 0;
+    const unsigned row_blocks = (unsigned)((M + 7) / 8);
+#define GBSP_TRY(x)              \
+    do {                         \
+        if ((st = (x))) goto out; \
+    } while (0)
+    GBSP_TRY(dev_alloc(&slot, (size_t)(nwin * nbc)));
+    GBSP_TRY(dev_alloc(&win_nb, (size_t)nwin + 1));
+    GBSP_TRY(dev_alloc(&padded, (size_t)nwin + 1));
+    GBSP_TRY(dev_alloc(&has, (size_t)nwin + 1));
+    GBSP_TRY(dev_alloc(&win_off, (size_t)nwin + 1));
+    GBSP_TRY(dev_alloc(&tc_index, (size_t)nwin + 1));
+    GBSP_TRY(dev_alloc(&res_len, (size_t)M + 1));
+    GBSP_TRY(dev_alloc(&flag, 1));
+    GBSP_TRY(dev_alloc(&p->err, 1));
+    cudaMemsetAsync(slot, 0, sizeof(int32_t) * (size_t)(nwin * nbc), s);
+    cudaMemsetAsync(flag, 0, sizeof(int), s);
+    cudaMemsetAsync(p->err, 0, sizeof(int), s);
+    if (M > 0) {
+        count_blocks_kernel<<<row_blocks, 256, 0, s>>>(A->rowptr, A->colidx, (int)M, (int)nbc, slot, flag);
+        mark_dense_kernel<<<(unsigned)nwin, 256, 0, s>>>(slot, (int)nbc, threshold, win_nb);
+        pad_counts_kernel<<<(unsigned)((nwin + 255) / 256), 256, 0, s>>>(win_nb, (int)nwin, padded, has);
+        count_launches(3);
+        GBSP_TRY(check_launch("plan count"));
+    }
+    GBSP_TRY(device_exclusive_scan(padded, win_off, nwin, s));
+    GBSP_TRY(device_exclusive_scan(has, tc_index, nwin, s));
+    cudaMemcpyAsync(&totals[0], win_off + nwin, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&totals[1], tc_index + nwin, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) GBSP_TRY(check_launch("plan sync"));
+    if (hflag) GBSP_TRY(fail(GBSP_ERR_UNSUPPORTED, "plan: column indices must be strictly increasing in every row"));
+    p->nblocks = totals[0];
+    p->nwin_tc = totals[1];
+    GBSP_TRY(dev_alloc(&p->blk_col, (size_t)p->nblocks));
+    GBSP_TRY(dev_alloc(&p->atiles, (size_t)(p->nblocks / kBlkPerCh) * kATile));
+    GBSP_TRY(dev_alloc(&p->tc_row0, (size_t)p->nwin_tc));
+    GBSP_TRY(dev_alloc(&p->tc_blk, (size_t)p->nwin_tc + 1));
+    cudaMemsetAsync(p->atiles, 0, (size_t)(p->nblocks / kBlkPerCh) * kATile, s);
+    cudaMemsetAsync(p->tc_blk, 0, sizeof(int32_t), s);
+    if (M > 0) {
+        fill_blocks_kernel<<<(unsigned)nwin, 256, 0, s>>>(slot, (int)nbc, win_off, win_nb, tc_index, p->blk_col,
+                                                          p->tc_row0, p->tc_blk);
+        fill_values_kernel<<<row_blocks, 256, 0, s>>>(A->rowptr, A->colidx, static_cast<const uint16_t *>(A->vals),
+                                                      (int)M, (int)nbc, slot, win_off, p->atiles, res_len);
+        count_launches(2);
+        GBSP_TRY(check_launch("plan fill"));
+    }
+    GBSP_TRY(dev_alloc(&p->res_rowptr, (size_t)M + 1));
+    GBSP_TRY(device_exclusive_scan(res_len, p->res_rowptr, M, s));
+    cudaMemcpyAsync(&totals[0], p->res_rowptr + M, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) GBSP_TRY(check_launch("plan sync"));
+    p->res_nnz = totals[0];
+    p->dense_nnz = p->nnz - p->res_nnz;
+    GBSP_TRY(dev_alloc(&p->res_colidx, (size_t)p->res_nnz));
+    GBSP_TRY(dev_alloc(&p->res_vals, (size_t)p->res_nnz));
+    if (M > 0) {
+        fill_residual_kernel<<<row_blocks, 256, 0, s>>>(A->rowptr, A->colidx, static_cast<const uint16_t *>(A->vals),
+                                                        (int)M, (int)nbc, slot, p->res_rowptr, p->res_colidx,
+                                                        p->res_vals);
+        count_launches(1);
+        GBSP_TRY(check_launch("plan residual"));
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) GBSP_TRY(check_launch("plan sync"));
+out:
+#undef GBSP_TRY
+    cudaFree(slot);
+    cudaFree(win_nb);
+    cudaFree(padded);
+    cudaFree(has);
+    cudaFree(win_off);
+    cudaFree(tc_index);
+    cudaFree(res_len);
+    cudaFree(flag);
+    if (st) {
+        plan_free(p);
+        return st;
+    }
+    *out = p;
+    return ok();
+}
+
+GBSP_EXPORT int gbsp_plan_execute(const gbsp_plan *p, const gbsp_dense *B, gbsp_dense *C, void *stream) {
+    if (!p || !B || !C) return fail(GBSP_ERR_INVALID_ARG, "plan execute: null argument");
+    if (B->dtype != GBSP_BF16 || C->dtype != GBSP_F32)
+        return fail(GBSP_ERR_UNSUPPORTED, "plan execute: B must be BF16 and C FP32");
+    if (B->rows != p->K || C->rows != p->M || C->cols != B->cols || B->ld < B->cols || C->ld < C->cols)
+        return fail(GBSP_ERR_INVALID_ARG, "plan execute: shape mismatch");
+    const int64_t N = B->cols;
+    if (p->nwin_tc > 0 && (N % 8 || B->ld % 8 || !aligned16(B->data) || N < 64 || N > 512))
+        return fail(GBSP_ERR_UNSUPPORTED, "plan execute: tensor-core tiles need 64 <= N <= 512, N and ld multiples "
+                                          "of 8 and a 16-byte aligned B");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // residual entries (and the overwrite of C) through the CSR kernels
+    gbsp_csr R{p->M, p->K, p->res_nnz, p->res_rowptr, p->res_colidx, p->res_vals, nullptr, GBSP_BF16};
+    int st = spmm_csr_ex(&R, B, C, &p->residual_opts, stream);
+    if (st) return st;
+    if (p->nwin_tc == 0 || N == 0) return ok();
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return fail(GBSP_ERR_CUDA, "plan execute: cuTensorMapEncodeTiled is not available");
+    CUtensorMap map;
+    const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)p->K};
+    const cuuint64_t strides[1] = {(cuuint64_t)B->ld * 2};
+    const cuuint32_t box[2] = {64, 8};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, B->data, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return fail(GBSP_ERR_CUDA, "plan execute: tensor map encoding failed");
+    TcArgs args{p->tc_row0, p->tc_blk, p->blk_col, p->atiles, static_cast<float *>(C->data), C->ld, (int)p->M,
+                (int)p->K, (int)N, p->err};
+    const int nt = (int)((N + 127) / 128);
+    switch (nt) {
+        case 1: st = launch_tc<1>(map, args, p->nwin_tc, s); break;
+        case 2: st = launch_tc<2>(map, args, p->nwin_tc, s); break;
+        case 3: st = launch_tc<3>(map, args, p->nwin_tc, s); break;
+        default: st = launch_tc<4>(map, args, p->nwin_tc, s); break;
+    }
+    return st ? st : ok();
+}
+
+GBSP_EXPORT int gbsp_plan_info(const gbsp_plan *p, int64_t *info, int n) {
+    if (!p || !info || n < 5) return fail(GBSP_ERR_INVALID_ARG, "plan info: need room for 5 values");
+    info[0] = p->nwin_tc;
+    info[1] = p->nblocks;
+    info[2] = p->dense_nnz;
+    info[3] = p->res_nnz;
+    info[4] = p->threshold;
+    return ok();
+}
+
+GBSP_EXPORT int gbsp_plan_check(const gbsp_plan *p, void *stream) {
+    if (!p) return fail(GBSP_ERR_INVALID_ARG, "plan check: null plan");
+    int h = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(&h, p->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return check_launch("plan check");
+    if (h) return fail(GBSP_ERR_TIMEOUT, "a tensor-core window gave up waiting (code %d)", h);
+    return ok();
+}
+
+GBSP_EXPORT void gbsp_plan_destroy(gbsp_plan *p) { plan_free(p); }

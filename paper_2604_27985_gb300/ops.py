@@ -59,9 +59,9 @@ def _dense(t: torch.Tensor, scale=None) -> Dense:
     return Dense(_ptr(t), t.shape[0], t.shape[1], _ld(t), _ptr(scale), _dtype(t))
 
 
-def _opts(variant="auto", validate=False, unroll=0, ctas_per_sm=0) -> Opts:
+def _opts(variant="auto", validate=False, unroll=0, ctas_per_sm=0, vecs=0) -> Opts:
     return Opts(VARIANTS[variant] if isinstance(variant, str) else int(variant), int(bool(validate)),
-                int(unroll), int(ctas_per_sm))
+                int(unroll), int(ctas_per_sm), int(vecs))
 
 
 def spmm_csr(rowptr, colidx, vals, B, C, M, K, N) -> None:
@@ -83,26 +83,26 @@ def sddmm_csr(rowptr, colidx, svals, X, Y, out, M, N, Kd) -> None:
 
 
 def spmm(rowptr, colidx, vals, B, out=None, *, a_scale=None, b_scale=None, variant="auto", unroll=0,
-         ctas_per_sm=0, validate=False, stream=None) -> torch.Tensor:
+         ctas_per_sm=0, vecs=0, validate=False, stream=None) -> torch.Tensor:
     """C = A B (Eq. 1) through spmm_csr_ex; returns the FP32 M x N result."""
     M = rowptr.numel() - 1
     if out is None:
         out = torch.empty((M, B.shape[1]), dtype=torch.float32, device=B.device)
     A = _csr(rowptr, colidx, vals, B.shape[0], a_scale)
     b, c = _dense(B, b_scale), _dense(out)
-    o = _opts(variant, validate, unroll, ctas_per_sm)
+    o = _opts(variant, validate, unroll, ctas_per_sm, vecs)
     check(lib.spmm_csr_ex(ctypes.byref(A), ctypes.byref(b), ctypes.byref(c), ctypes.byref(o), _stream(stream)))
     return out
 
 
 def sddmm(rowptr, colidx, svals, X, Y, out=None, *, x_scale=None, y_scale=None, variant="auto",
-          validate=False, stream=None) -> torch.Tensor:
+          vecs=0, validate=False, stream=None) -> torch.Tensor:
     """out[p] = s_p <X_i, Y_j> (Eq. 2) through sddmm_csr_ex; returns FP32 out[nnz]."""
     if out is None:
         out = torch.empty(colidx.numel(), dtype=torch.float32, device=X.device)
     S = _csr(rowptr, colidx, svals, Y.shape[0])
     x, y = _dense(X, x_scale), _dense(Y, y_scale)
-    o = _opts(variant, validate)
+    o = _opts(variant, validate, vecs=vecs)
     check(lib.sddmm_csr_ex(ctypes.byref(S), ctypes.byref(x), ctypes.byref(y), _ptr(out), ctypes.byref(o),
                            _stream(stream)))
     return out
@@ -149,3 +149,97 @@ def sm_count() -> int:
 def launch_count() -> int:
     """Kernels launched by the library so far in this process."""
     return int(lib.gbsp_launch_count())
+
+
+class TcPlan:
+    """Condensed-tile tensor-core plan of a BF16 CSR matrix (gbsp_plan_create): dense 16 x 8
+    blocks run on tcgen05, the rest on the CSR kernels.  ``execute(B)`` returns C = A B."""
+
+    def __init__(self, rowptr, colidx, vals, ncols, threshold=0, *, residual_variant="auto", residual_vecs=0,
+                 residual_unroll=0, stream=None):
+        self.M = rowptr.numel() - 1
+        self.K = int(ncols)
+        A = _csr(rowptr, colidx, vals, ncols)
+        o = _opts(residual_variant, False, residual_unroll, 0, residual_vecs)
+        h = ctypes.c_void_p()
+        check(lib.gbsp_plan_create(ctypes.byref(A), int(threshold), ctypes.byref(o), _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    def execute(self, B, out=None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.M, B.shape[1]), dtype=torch.float32, device=B.device)
+        b, c = _dense(B), _dense(out)
+        check(lib.gbsp_plan_execute(self._h, ctypes.byref(b), ctypes.byref(c), _stream(stream)))
+        return out
+
+    def info(self) -> dict:
+        arr = (ctypes.c_int64 * 5)()
+        check(lib.gbsp_plan_info(self._h, arr, 5))
+        return {"dense_windows": arr[0], "dense_blocks": arr[1], "dense_nnz": arr[2], "residual_nnz": arr[3],
+                "threshold": arr[4]}
+
+    def check(self, stream=None) -> None:
+        check(lib.gbsp_plan_check(self._h, _stream(stream)))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib.gbsp_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _gnn_arrays(graphs):
+    """graphs: list of (rowptr, colidx, svals, H, O, E) CUDA tensors (H, O BF16; E float32)."""
+    G = len(graphs)
+    S = (Csr * max(G, 1))()
+    Hd = (Dense * max(G, 1))()
+    Od = (Dense * max(G, 1))()
+    E = (ctypes.c_void_p * max(G, 1))()
+    for g, (rp, ci, sv, H, O, Ev) in enumerate(graphs):
+        S[g] = _csr(rp, ci, sv, rp.numel() - 1)
+        Hd[g] = _dense(H)
+        Od[g] = _dense(O)
+        E[g] = _ptr(Ev)
+    return G, S, Hd, E, Od
+
+
+class GnnPlan:
+    """Batched SDDMM -> SpMM chain over many graphs as one persistent launch replayed from a
+    CUDA graph (gbsp_gnn_plan_create).  ``execute()`` fills every graph's E and O."""
+
+    def __init__(self, graphs, edges_per_tile=0, stream=None):
+        self._keep = graphs  # the plan holds raw pointers into these tensors
+        G, S, Hd, E, Od = _gnn_arrays(graphs)
+        h = ctypes.c_void_p()
+        check(lib.gbsp_gnn_plan_create(G, S, Hd, E, Od, int(edges_per_tile), _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    def execute(self, stream=None) -> None:
+        check(lib.gbsp_gnn_plan_execute(self._h, _stream(stream)))
+
+    def info(self) -> dict:
+        arr = (ctypes.c_int64 * 4)()
+        check(lib.gbsp_gnn_plan_info(self._h, arr, 4))
+        return {"graphs": arr[0], "tiles": arr[1], "rows": arr[2], "edges": arr[3]}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib.gbsp_gnn_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gnn_sddmm_spmm_batched(graphs, stream=None) -> None:
+    """One-shot batched chain (creates, runs and destroys a plan; synchronises)."""
+    G, S, Hd, E, Od = _gnn_arrays(graphs)
+    check(lib.gnn_sddmm_spmm_batched(G, S, Hd, E, Od, _stream(stream)))

@@ -74,7 +74,9 @@ def test_argument_errors_return_without_launching(gb):
     B = _lib.Dense(16, 5, 8, 8, None, _lib.BF16)  # dtype mismatch with A
     assert lib.spmm_csr_ex(P(A), P(B), P(C), None, None) == -4
     B = _lib.Dense(16, 5, 8, 8, None, _lib.F32)
-    o = _lib.Opts(1, 0, 3, 0)  # unroll 3 is not offered
+    o = _lib.Opts(1, 0, 3, 0, 0)  # unroll 3 is not offered
+    assert lib.spmm_csr_ex(P(A), P(B), P(C), P(o), None) == -1
+    o = _lib.Opts(1, 0, 2, 0, 3)  # 3 vectors per lane are not offered
     assert lib.spmm_csr_ex(P(A), P(B), P(C), P(o), None) == -1
     E = _lib.Dense(16, 5, 8, 8, None, _lib.E4M3)  # E4M3 without row scales
     assert lib.spmm_csr_ex(P(A), P(E), P(C), None, None) == -1

@@ -73,15 +73,17 @@ def test_spmm_fp32(gb, name, N, variant):
     assert_within(C, ref, scale, TOL, f"{name} N={N} {variant}")
 
 
+@pytest.mark.parametrize("vecs", [1, 2, 4])
 @pytest.mark.parametrize("unroll", [1, 2, 4, 8])
 @pytest.mark.parametrize("variant", ["rowsplit", "merge"])
-def test_spmm_unroll(gb, unroll, variant):
+def test_spmm_layouts(gb, vecs, unroll, variant):
+    """Every (vectors per lane, gathers in flight) layout on full and partial column tiles."""
     A = mat("powerlaw")
-    for N in (8, 64, 128):
+    for N in (8, 64, 96, 128, 264):
         B = gen.dense_normal(A.K, N, 12)
-        C = run_spmm(gb, A, B, variant=variant, unroll=unroll)
+        C = run_spmm(gb, A, B, variant=variant, unroll=unroll, vecs=vecs)
         ref, scale = oracle.spmm(A.rowptr, A.colidx, A.vals, B)
-        assert_within(C, ref, scale, TOL, f"unroll={unroll} N={N}")
+        assert_within(C, ref, scale, TOL, f"vecs={vecs} unroll={unroll} N={N}")
 
 
 @pytest.mark.parametrize("ctas", [1, 2, 7])
@@ -187,12 +189,28 @@ def run_sddmm(gb, S, X, Y, **kw):
 
 @pytest.mark.parametrize("name", list(MATS))
 @pytest.mark.parametrize("Kd", [2, 4, 8, 16, 32, 36, 64, 128, 256, 512, 33])
-def test_sddmm_fp32(gb, name, Kd):
+@pytest.mark.parametrize("variant", ["auto", "merge"])
+def test_sddmm_fp32(gb, name, Kd, variant):
     S = mat(name)
     X, Y = gen.dense_normal(S.M, Kd, 41), gen.dense_normal(S.K, Kd, 42)
-    out = run_sddmm(gb, S, X, Y)
+    if variant == "merge" and Kd % 4:
+        with pytest.raises(gb.GbspError, match="ALIGN"):
+            run_sddmm(gb, S, X, Y, variant=variant)
+        return
+    out = run_sddmm(gb, S, X, Y, variant=variant)
     ref, scale = oracle.sddmm(S.rowptr, S.colidx, S.vals, X, Y)
-    assert_within(out, ref, scale, TOL, f"{name} Kd={Kd}")
+    assert_within(out, ref, scale, TOL, f"{name} Kd={Kd} {variant}")
+
+
+@pytest.mark.parametrize("vecs", [1, 2, 4])
+@pytest.mark.parametrize("Kd", [8, 32, 40, 128, 256, 512])
+@pytest.mark.parametrize("variant", ["rowsplit", "merge"])
+def test_sddmm_layouts(gb, vecs, Kd, variant):
+    S = mat("powerlaw")
+    X, Y = gen.dense_normal(S.M, Kd, 51), gen.dense_normal(S.K, Kd, 52)
+    out = run_sddmm(gb, S, X, Y, vecs=vecs, variant=variant)
+    ref, scale = oracle.sddmm(S.rowptr, S.colidx, S.vals, X, Y)
+    assert_within(out, ref, scale, TOL, f"vecs={vecs} Kd={Kd}")
 
 
 @pytest.mark.parametrize("Kd", [8, 32, 128])
@@ -254,6 +272,9 @@ def test_validate(gb):
     assert gb.csr_validate(dev(bad_rp), dev(A.colidx), A.K) == 1
     with pytest.raises(gb.GbspError, match="INVALID_CSR"):
         gb.spmm(dev(A.rowptr), dev(bad_ci), dev(A.vals), dev(gen.dense_normal(A.K, 8, 1)), validate=True)
+    with pytest.raises(gb.GbspError, match="INVALID_CSR"):
+        X = dev(gen.dense_normal(A.M, 8, 2))
+        gb.sddmm(dev(A.rowptr), dev(bad_ci), dev(A.vals), X, dev(gen.dense_normal(A.K, 8, 3)), validate=True)
 
 
 # ---- the benchmark's workload, in the benchmark's launch configuration ---------------------

@@ -91,10 +91,11 @@ def mat(k):
 @pytest.mark.parametrize("struct", list(STRUCTS))
 @pytest.mark.parametrize("N", [64, 256, 136])
 @pytest.mark.parametrize("variant", ["rowsplit", "merge"])
-def test_spmm_bf16(gb, struct, N, variant):
+@pytest.mark.parametrize("vecs", [1, 2])
+def test_spmm_bf16(gb, struct, N, variant, vecs):
     A = mat(struct)
     B = gen.dense_normal(A.K, N, 14)
-    C = _spmm_bf16(gb, A, B, variant=variant)
+    C = _spmm_bf16(gb, A, B, variant=variant, vecs=vecs)
     da = oracle.bf16_decode(oracle.bf16_round(A.vals))
     db = oracle.bf16_decode(oracle.bf16_round(B))
     ref, sc = oracle.spmm(A.rowptr, A.colidx, da, db)
@@ -157,11 +158,12 @@ def test_spmm_lowp_integers_bit_exact(gb, variant):
 # ---- SDDMM -----------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("Kd", [32, 128, 256, 40])
-def test_sddmm_bf16(gb, Kd):
+@pytest.mark.parametrize("variant", ["rowsplit", "merge"])
+def test_sddmm_bf16(gb, Kd, variant):
     S = mat("uniform")
     X, Y = gen.dense_normal(S.M, Kd, 21), gen.dense_normal(S.K, Kd, 22)
     out = gb.sddmm(dev(S.rowptr), dev(S.colidx), dev(S.vals), gb.quantize_bf16(dev(X)),
-                   gb.quantize_bf16(dev(Y))).cpu().numpy()
+                   gb.quantize_bf16(dev(Y)), variant=variant).cpu().numpy()
     dx, dy = oracle.bf16_decode(oracle.bf16_round(X)), oracle.bf16_decode(oracle.bf16_round(Y))
     ref, sc = oracle.sddmm(S.rowptr, S.colidx, S.vals, dx, dy)
     assert_within(out, ref, sc, TOL32, f"bf16 dequantised Kd={Kd}")
@@ -170,12 +172,14 @@ def test_sddmm_bf16(gb, Kd):
 
 
 @pytest.mark.parametrize("Kd", [32, 128, 256, 48])
-def test_sddmm_e4m3(gb, Kd):
+@pytest.mark.parametrize("variant", ["rowsplit", "merge"])
+def test_sddmm_e4m3(gb, Kd, variant):
     S = mat("clustered")
     X, Y = gen.dense_normal(S.M, Kd, 23), gen.dense_normal(S.K, Kd, 24)
     qx, u = gb.quantize_e4m3_rows(dev(X))
     qy, w = gb.quantize_e4m3_rows(dev(Y))
-    out = gb.sddmm(dev(S.rowptr), dev(S.colidx), dev(S.vals), qx, qy, x_scale=u, y_scale=w).cpu().numpy()
+    out = gb.sddmm(dev(S.rowptr), dev(S.colidx), dev(S.vals), qx, qy, x_scale=u, y_scale=w,
+                   variant=variant).cpu().numpy()
     oqx, ou = oracle.e4m3_rows(X)
     oqy, ow = oracle.e4m3_rows(Y)
     ref, sc = oracle.sddmm(S.rowptr, S.colidx, S.vals, oracle.e4m3_rows_dequant(oqx, ou),
