@@ -270,23 +270,19 @@ def run_ours(args):
     spmm_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
     sddmm_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
 
-    # end to end through the public API with host buffers: pinned host -> device copies of
-    # this step's inputs, the two calls, device -> pinned host copies of both results.
-    h_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (A.rowptr, A.colidx, A.vals, B, X, Y)]
-    d_in = [torch.empty_like(h, device=dev) for h in h_in]
+    # end to end through the public API with host buffers: the library's host-resident entry
+    # point streams this step's inputs from pinned host memory in row chunks, computes both
+    # products and streams C and out back, all inside the timed region.
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_rp, h_ci, h_v, h_B, h_X, h_Y = (pin(a) for a in (A.rowptr, A.colidx, A.vals, B, X, Y))
     h_C = torch.empty((M, N_SPMM), dtype=torch.float32).pin_memory()
     h_out = torch.empty(nnz, dtype=torch.float32).pin_memory()
-    h2d = sum(h.numel() * h.element_size() for h in h_in)
+    h2d = sum(h.numel() * h.element_size() for h in (h_rp, h_ci, h_v, h_B, h_X, h_Y))
     d2h = h_C.numel() * 4 + h_out.numel() * 4
 
     def e2e_step():
-        for d, h in zip(d_in, h_in):
-            d.copy_(h, non_blocking=True)
-        drp, dci, dv, dB, dX, dY = d_in
-        gb.spmm(drp, dci, dv, dB, out=C, stream=stream)
-        gb.sddmm(drp, dci, dv, dX, dY, out=out, stream=stream)
-        h_C.copy_(C, non_blocking=True)
-        h_out.copy_(out, non_blocking=True)
+        gb.spmm_sddmm_host(h_rp, h_ci, h_v, B=h_B, C=h_C, X=h_X, Y=h_Y, out=h_out, chunks=args.e2e_chunks,
+                           slots=3, stream=stream)
 
     for _ in range(max(1, args.warmup)):
         e2e_step()
@@ -360,6 +356,170 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ---- the other hot-path rows: one JSON line each (python bench.py --workload ...) ----------
+
+def _event_ms(fn, steps, warmup, stream):
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _line(metric, value, unit, ms, args, dtype, config, **extra):
+    out = {"metric": metric, "value": round(value, 3), "unit": unit, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": dtype, "data": "synthetic (seeded generators; no dataset)",
+           "config": config}
+    out.update(extra)
+    print(json.dumps(out), flush=True)
+
+
+def run_precision(args):
+    """16,384^2 at 90%, N = Kd = 256: SpMM + SDDMM in FP32, BF16, E4M3 (CUDA cores) and the
+    BF16 condensed-tile tensor-core plan, on the uniform and the clustered layouts."""
+    import torch
+
+    import paper_2604_27985_gb300 as gb
+
+    dev = torch.device("cuda")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    stream = torch.cuda.current_stream()
+    peak, _ = peaks()
+    forms = {}
+    for layout in ("uniform", "clustered"):
+        A = (gen.csr_uniform(16384, 16384, 0.9, seed=2001) if layout == "uniform"
+             else gen.csr_clustered(16384, 16384, 0.9, seed=2002))
+        B, X, Y = (gen.dense_normal(16384, 256, 2003 + k) for k in range(3))
+        rp, ci, v = t(A.rowptr), t(A.colidx), t(A.vals)
+        Bd, Xd, Yd = t(B), t(X), t(Y)
+        C = torch.empty((A.M, 256), device=dev)
+        out = torch.empty(A.nnz, device=dev)
+        qa, qb, qx, qy = gb.quantize_bf16(v), gb.quantize_bf16(Bd), gb.quantize_bf16(Xd), gb.quantize_bf16(Yd)
+        ea, sa = gb.quantize_e4m3_rows(v, rp)
+        eb, sb = gb.quantize_e4m3_rows(Bd)
+        ex, ux = gb.quantize_e4m3_rows(Xd)
+        ey, uy = gb.quantize_e4m3_rows(Yd)
+        plan = gb.TcPlan(rp, ci, qa, A.K)
+        info = plan.info()
+        runs = {
+            "fp32": (lambda: gb.spmm(rp, ci, v, Bd, out=C), lambda: gb.sddmm(rp, ci, v, Xd, Yd, out=out), 4, 4),
+            "bf16": (lambda: gb.spmm(rp, ci, qa, qb, out=C), lambda: gb.sddmm(rp, ci, v, qx, qy, out=out), 2, 2),
+            "e4m3": (lambda: gb.spmm(rp, ci, ea, eb, out=C, a_scale=sa, b_scale=sb),
+                     lambda: gb.sddmm(rp, ci, v, ex, ey, out=out, x_scale=ux, y_scale=uy), 1, 1),
+            "tc_bf16": (lambda: plan.execute(qb, out=C), lambda: gb.sddmm(rp, ci, v, qx, qy, out=out), 2, 2),
+        }
+        for name, (f_spmm, f_sddmm, vb, eb_) in runs.items():
+            ms_a = _event_ms(f_spmm, args.steps, args.warmup, stream)
+            ms_b = _event_ms(f_sddmm, args.steps, args.warmup, stream)
+            gbytes = (A.nnz * (4 + vb + 256 * eb_) + A.M * (4 + 4 * 256)) / 1e9
+            forms[f"{layout}/{name}"] = {
+                "spmm_ms": round(ms_a, 4), "sddmm_ms": round(ms_b, 4),
+                "spmm_gflops": round(2 * A.nnz * 256 / ms_a / 1e6, 1),
+                "sddmm_gflops": round(2 * A.nnz * 256 / ms_b / 1e6, 1),
+                "step_gflops": round(4 * A.nnz * 256 / (ms_a + ms_b) / 1e6, 1),
+                "spmm_gather_frac": round(gbytes / (ms_a / 1e3) / peak, 3)}
+        forms[f"{layout}/tc_plan"] = info
+        plan.check()
+        plan.close()
+    best = max((k for k in forms if "/" in k and not k.endswith("tc_plan")), key=lambda k: forms[k]["step_gflops"])
+    base = forms["clustered/fp32"]["spmm_ms"] + forms["clustered/fp32"]["sddmm_ms"]
+    _line("SpMM & SDDMM GFLOP/s (2*nnz*N each), precision forms vs plain FP32", forms[best]["step_gflops"],
+          "GFLOP/s", forms[best]["spmm_ms"] + forms[best]["sddmm_ms"], args, best.split("/")[1],
+          {"workload": "CSR 16384x16384 at 90% (uniform seed 2001, clustered 16x8 blocks at 40% fill seed 2002), "
+                       "SpMM N=256 + SDDMM Kd=256", "best_form": best,
+           "fp32_clustered_step_ms": round(base, 4)}, forms=forms)
+
+
+def run_gnn(args):
+    """512 graphs (1,000..50,000 nodes, power-law degrees with mean 16), BF16 features of
+    width 64/128/256: SDDMM -> SpMM per graph in one persistent launch from a CUDA graph."""
+    import torch
+
+    import paper_2604_27985_gb300 as gb
+
+    dev = torch.device("cuda")
+    graphs = gen.gnn_batch(G=512, seed=3000)
+    devs, flop, gbytes = [], 0.0, 0.0
+    for k, (A, N) in enumerate(graphs):
+        H = torch.from_numpy(gen.dense_normal(A.M, N, 3000 * 1000 + k)).to(torch.bfloat16).to(dev)
+        devs.append((torch.from_numpy(A.rowptr).to(dev), torch.from_numpy(A.colidx).to(dev),
+                     torch.from_numpy(A.vals).to(dev), H, torch.empty_like(H),
+                     torch.empty(A.nnz, dtype=torch.float32, device=dev)))
+        flop += 4.0 * A.nnz * N
+        gbytes += (A.nnz * (4 + 4 + 4 + 2 * N) + A.M * (4 + 2 * N + 2 * N)) / 1e9
+    plan = gb.GnnPlan(devs)
+    stream = torch.cuda.current_stream()
+    launches0 = gb.launch_count()
+    ms = _event_ms(plan.execute, args.steps, args.warmup, stream)
+    launches = (gb.launch_count() - launches0) // (args.steps + args.warmup)
+    peak, _ = peaks()
+    info = plan.info()
+    _line("batched SDDMM->SpMM GFLOP/s (4*nnz*N over the batch)", flop / ms / 1e6, "GFLOP/s", ms, args, "bf16",
+          {"workload": "512 graphs, nodes log-uniform [1000, 50000], power-law degree (mean 16, max 2048), "
+                       "row-normalised values, BF16 features N in {64,128,256}, seed 3000", **info},
+          roofline={"bound": "hbm", "kernel": "gnn_kernel, gather model", "achieved": round(gbytes / ms * 1e3, 1),
+                    "peak": peak, "unit": "GB/s", "frac": round(gbytes / ms * 1e3 / peak, 4),
+                    "algorithmic_bytes_per_launch": int(gbytes * 1e9)},
+          gpu_launches_per_step=int(launches))
+
+
+def run_selector(args):
+    """Learned selector: 2,000 training and 200 held-out corpus matrices, labels from the
+    exhaustive autotuner, the MLP trained by the library's kernels; regret vs exhaustive."""
+    import torch
+
+    import paper_2604_27985_gb300 as gb
+    from paper_2604_27985_gb300 import selector as sel
+
+    n_train, n_test = args.selector_train, args.selector_test
+    feats, times, specs = [], [], []
+    t_label = time.time()
+    for i in range(n_train + n_test):
+        spec = gen.corpus_spec(i, 5000 if i < n_train else 6000)
+        rp, ci, v = gen.corpus_matrix(spec)
+        f, tm = sel.label(rp, ci, v, spec["n"], spec["N"], spec["dtype"], reps=3)
+        feats.append(f.cpu().numpy())
+        times.append(tm)
+        specs.append(spec)
+    t_label = time.time() - t_label
+    feats, times = np.stack(feats), np.asarray(times)
+    model = sel.Selector(seed=0)
+    t0 = time.time()
+    model.fit(feats[:n_train], times[:n_train], steps=args.selector_steps, batch=64, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    _, choice = model.predict(feats[n_train:])
+    r = sel.regret(times[n_train:], choice.cpu().numpy())
+    fixed_all = [float(np.mean(sel.regret(times[n_train:], np.full(n_test, v)))) for v in range(gb.N_VARIANTS)]
+    fixed = {"best_single_variant": int(np.argmin(fixed_all)), "best_single_mean": min(fixed_all),
+             "rowsplit_v2_u4": fixed_all[4], "merge_v2_u4": fixed_all[13]}
+    # time of one selection (features + inference) on a held-out matrix
+    spec = specs[n_train]
+    rp, ci, v = gen.corpus_matrix(spec)
+    ms_sel = _event_ms(lambda: model.choose(rp, ci, spec["n"], spec["N"], spec["dtype"]), 20, 3,
+                       torch.cuda.current_stream())
+    if args.selector_save:
+        model.save(args.selector_save, regret_mean=float(r.mean()), regret_p90=float(np.quantile(r, 0.9)),
+                   regret_max=float(r.max()), train=n_train, test=n_test)
+    _line("selector regret vs exhaustive autotuning (mean t_chosen/t_best - 1)", float(r.mean()), "fraction",
+          ms_sel, args, "f32",
+          {"workload": f"corpus of {n_train} training + {n_test} held-out matrices (rows log-uniform "
+                       "[4096, 262144], sparsity 90/99/99.9%, uniform/power-law/banded/block, N 32..512, "
+                       "FP32/BF16), 24 SpMM variants", "redraws": int(sum(s["redraws"] for s in specs))},
+          higher_is_better=False, regret={"mean": float(r.mean()), "p50": float(np.median(r)),
+                                          "p90": float(np.quantile(r, 0.9)), "max": float(r.max()),
+                                          "fixed_choices_mean": fixed},
+          seconds={"labels": round(t_label, 1), "train": round(t_train, 2)}, selection_ms=round(ms_sel, 4))
 
 
 def _sub(A, r0, r1):
@@ -442,6 +602,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-chunks", type=int, default=16)
+    ap.add_argument("--workload", default="csr65536", choices=["csr65536", "precision", "gnn", "selector"])
+    ap.add_argument("--selector-train", type=int, default=2000)
+    ap.add_argument("--selector-test", type=int, default=200)
+    ap.add_argument("--selector-steps", type=int, default=6000)
+    ap.add_argument("--selector-save", default="")
     ap.add_argument("--write-traffic", nargs=3, metavar=("REPORT", "SPMM_RE", "SDDMM_RE"),
                     help="store per-launch DRAM bytes from an ncu report and exit")
     args = ap.parse_args()
@@ -452,6 +618,12 @@ def main():
         ap.error("at least 3 warm-up steps")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "precision":
+        run_precision(args)
+    elif args.workload == "gnn":
+        run_gnn(args)
+    elif args.workload == "selector":
+        run_selector(args)
     else:
         run_ours(args)
 

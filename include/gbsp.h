@@ -140,6 +140,22 @@ int gbsp_quantize_bf16(const float *x, uint16_t *out, int64_t n, void *stream);
 int gbsp_quantize_e4m3_rows(const float *x, const int32_t *rowptr, int64_t nrows, int64_t ncols,
                             int64_t ld, uint8_t *q, float *scale, void *stream);
 
+/* ---- host-resident operands, streamed in row chunks ----------------------------------------- */
+
+/* SpMM (Eq. 1, when B, C and N > 0 are given) and / or SDDMM (Eq. 2, when X, Y, out and
+ * Kd > 0 are given) on FP32 operands in HOST memory (pinned memory lets the copies overlap
+ * the kernels): rowptr[M+1], colidx[nnz], vals[nnz] (also the S values of SDDMM), B[K x N],
+ * C[M x N], X[M x Kd], Y[K x Kd], out[nnz], all row-major with ld = width.  The library
+ * copies B, X, Y once, then streams the matrix in `chunks` row chunks of about equal
+ * entries (default 8 when < 1) through `slots` device buffers (default 2 when < 2) on its
+ * own copy-in, compute and copy-out streams, so chunk i+1 arrives while chunk i computes and
+ * chunk i-1's results return.  Device workspace comes from the library's pool.  The call
+ * returns once everything is queued; `stream` (the caller's) waits for the last result, so
+ * synchronise it before reading C and out.  N and Kd must be multiples of 4. */
+int gbsp_spmm_sddmm_host(const int32_t *rowptr, const int32_t *colidx, const float *vals, const float *B,
+                         float *C, int64_t N, const float *X, const float *Y, float *out, int64_t Kd, int64_t M,
+                         int64_t K, int64_t nnz, int32_t chunks, int32_t slots, void *stream);
+
 /* ---- condensed-tile tensor-core plan (BF16) ----------------------------------------------- */
 
 /* A plan splits a BF16 CSR matrix A into dense 16 x 8 blocks (aligned; at least `threshold`
@@ -188,6 +204,49 @@ int gbsp_gnn_plan_info(const gbsp_gnn_plan *plan, int64_t *info, int n);
 void gbsp_gnn_plan_destroy(gbsp_gnn_plan *plan);
 int gnn_sddmm_spmm_batched(int G, const gbsp_csr *S, const gbsp_dense *H, float *const *E, gbsp_dense *O,
                            void *stream);
+
+/* ---- kernel selection: features, autotuner, MLP ------------------------------------------- */
+
+/* The 24 SpMM variants the selector chooses among, as options for spmm_csr_ex:
+ *   0..8   row-split, vecs {1,2,4} x unroll {2,4,8}     (index = 3 * vecs_index + unroll_index)
+ *   9..17  merge path, the same nine layouts
+ *   18..21 merge path with 1 or 2 CTAs per SM, vecs {1,2}, unroll 4
+ *   22     unvectorised; 23 row-split with vecs 1, unroll 1. */
+int gbsp_variant_opts(int variant, gbsp_opts *out);
+
+/* 16 features of a CSR matrix for a dense width N and dtype, written to feats (device,
+ * float[16]) in one pass over rowptr / colidx (asynchronous):
+ *   0 log2 M, 1 log2 K, 2 log2(1 + nnz), 3 log2(density), 4 log2(1 + mean row length),
+ *   5 log2(1 + row-length standard deviation), 6 its coefficient of variation,
+ *   7 log2(1 + max row length), 8 max / mean row length, 9 fraction of empty rows,
+ *   10 mean |j - floor(i K / M)| / K, 11 max of the same / K, 12 fraction of consecutive
+ *   entries of a row less than 8 columns apart, 13 fraction of entries whose column is also
+ *   stored in the next row (rows sorted by column), 14 log2 N, 15 dtype. */
+int gbsp_features(const gbsp_csr *A, int64_t N, int32_t dtype, float *feats, void *stream);
+
+/* norm[0..15] = mean, norm[16..31] = standard deviation (1 where 0) of n feature rows. */
+int gbsp_feature_norm(const float *feats, int n, float *norm, void *stream);
+
+/* MLP 16 -> 64 -> 64 -> 24 with ReLU on the hidden layers; weights (device, 6,808 floats)
+ * laid out W1[64x16], b1[64], W2[64x64], b2[64], W3[24x64], b3[24] (row-major, out x in);
+ * inputs standardised with norm.  out (n x 24, may be NULL) receives the predictions, choice
+ * (n, may be NULL) the index of the smallest. */
+int gbsp_mlp_predict(const float *weights, const float *norm, const float *feats, int n, float *out,
+                     int32_t *choice, void *stream);
+
+/* `steps` Adam steps (beta 0.9 / 0.999, eps 1e-8, learning rate lr) of the masked squared
+ * error sum(mask (y - target)^2) / sum(mask) over minibatches of `batch` (<= 64) samples
+ * taken in turn from order[0..norder) (wrapping); adam holds the first then the second
+ * moments (2 x 6,808 floats); t0 = steps already taken.  One CTA, deterministic. */
+int gbsp_mlp_train(float *weights, float *adam, const float *norm, const float *feats, const float *targets,
+                   const float *mask, const int32_t *order, int norder, int steps, int batch, float lr, int t0,
+                   void *stream);
+
+/* Times every variant of spmm_csr_ex on A, B, C (one untimed call, then reps timed calls
+ * with CUDA events) and writes times_ms[24] (host; INFINITY where a variant does not apply)
+ * and *best (host).  Synchronises the stream; C ends up holding the last variant's result. */
+int gbsp_autotune(const gbsp_csr *A, const gbsp_dense *B, gbsp_dense *C, int reps, float *times_ms,
+                  int32_t *best, void *stream);
 
 /* ---- allocation-free variant ---------------------------------------------------------- */
 

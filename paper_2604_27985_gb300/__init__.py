@@ -6,6 +6,14 @@ the library is not built: there is no CPU fallback.
 """
 from ._lib import GbspError, LIB_PATH  # noqa: F401
 from .ops import (  # noqa: F401
+    N_PARAMS,
+    N_VARIANTS,
+    autotune,
+    feature_norm,
+    features,
+    mlp_predict,
+    mlp_train,
+    variant_options,
     GnnPlan,
     gnn_sddmm_spmm_batched,
     TcPlan,
@@ -19,4 +27,5 @@ from .ops import (  # noqa: F401
     spmm,
     spmm_csr,
     spmm_csr_noalloc,
+    spmm_sddmm_host,
 )

@@ -74,6 +74,15 @@ def _load() -> ctypes.CDLL:
         "gbsp_gnn_plan_info": [P, ctypes.POINTER(I64), I],
         "gnn_sddmm_spmm_batched": [I, ctypes.POINTER(Csr), ctypes.POINTER(Dense), ctypes.POINTER(P),
                                    ctypes.POINTER(Dense), P],
+        "gbsp_variant_opts": [I, ctypes.POINTER(Opts)],
+        "gbsp_features": [ctypes.POINTER(Csr), I64, ctypes.c_int32, P, P],
+        "gbsp_feature_norm": [P, I, P, P],
+        "gbsp_mlp_predict": [P, P, P, I, P, P, P],
+        "gbsp_mlp_train": [P, P, P, P, P, P, P, I, I, I, ctypes.c_float, I, P],
+        "gbsp_autotune": [ctypes.POINTER(Csr), ctypes.POINTER(Dense), ctypes.POINTER(Dense), I,
+                          ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int32), P],
+        "gbsp_spmm_sddmm_host": [P, P, P, P, P, I64, P, P, P, I64, I64, I64, I64, ctypes.c_int32, ctypes.c_int32,
+                                 P],
         "gbsp_get_last_error": [],
         "gbsp_device_sm_count": [],
     }

@@ -1,0 +1,191 @@
+// Host-resident SpMM / SDDMM: the CSR streams to the device in row chunks while earlier
+// chunks compute and their results stream back, the GPU counterpart of the paper's
+// streamed A with results copied back per chunk (Section III-A) and of its overlap of
+// transfers with computation (Section III-A-2, multiple accumulator rows).
+//
+// Three streams: host-to-device copies, kernels, device-to-host copies.  Each chunk of
+// rows goes through one of `slots` device buffers (row pointers, column indices, values,
+// its C rows and its SDDMM outputs); events order copy -> compute -> copy-back per chunk,
+// and a slot is refilled only after its previous chunk's results have left the device.  The
+// dense operands (B for SpMM, X and Y for SDDMM) are copied once at the start.  Column
+// indices and values of chunk [r0, r1) sit at device offset 0 while the kernels index
+// them with the matrix's absolute entry numbers, so the kernels get base pointers moved
+// back by rowptr[r0].
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace gbsp {
+namespace {
+
+struct Slot {
+    int32_t *rowptr = nullptr, *colidx = nullptr;
+    float *vals = nullptr, *C = nullptr, *out = nullptr;
+    cudaEvent_t copied = nullptr, computed = nullptr, drained = nullptr;
+};
+
+}  // namespace
+}  // namespace gbsp
+
+using namespace gbsp;
+
+GBSP_EXPORT int gbsp_spmm_sddmm_host(const int32_t *rowptr, const int32_t *colidx, const float *vals,
+                                     const float *B, float *C, int64_t N, const float *X, const float *Y,
+                                     float *out, int64_t Kd, int64_t M, int64_t K, int64_t nnz, int32_t chunks,
+                                     int32_t slots, void *stream) {
+    const bool do_spmm = B && C && N > 0, do_sddmm = X && Y && out && Kd > 0;
+    if (M < 0 || K < 0 || nnz < 0 || M > 2147483647LL || K > 2147483647LL || nnz > 2147483647LL ||
+        (M > 0 && !rowptr) || (nnz > 0 && (!colidx || !vals)) || N < 0 || Kd < 0)
+        return fail(GBSP_ERR_INVALID_ARG, "host pipeline: bad arguments");
+    if (!do_spmm && !do_sddmm) return ok();
+    if ((do_spmm && N % 4) || (do_sddmm && Kd % 4))
+        return fail(GBSP_ERR_ALIGN, "host pipeline: N and Kd must be multiples of 4");
+    if (M == 0) return ok();
+    if (chunks < 1) chunks = 8;
+    if (chunks > M) chunks = (int32_t)M;
+    if (slots < 2) slots = 2;
+    if (slots > chunks) slots = chunks;
+    cudaStream_t user = static_cast<cudaStream_t>(stream);
+    // chunk boundaries with about equal entries
+    std::vector<int64_t> bounds(1, 0);
+    for (int c = 1; c < chunks; ++c) {
+        const int64_t want = nnz * c / chunks;
+        int64_t lo = bounds.back() + 1, hi = M - (chunks - c);
+        while (lo < hi) {  // first row whose start reaches `want`
+            const int64_t mid = (lo + hi) / 2;
+            if (rowptr[mid] < want) lo = mid + 1;
+            else hi = mid;
+        }
+        bounds.push_back(lo);
+    }
+    bounds.push_back(M);
+    int64_t max_rows = 0, max_nnz = 0;
+    for (int c = 0; c < chunks; ++c) {
+        max_rows = std::max(max_rows, bounds[c + 1] - bounds[c]);
+        max_nnz = std::max(max_nnz, (int64_t)(rowptr[bounds[c + 1]] - rowptr[bounds[c]]));
+    }
+    cudaStream_t s_in = nullptr, s_run = nullptr, s_out = nullptr;
+    std::vector<Slot> sl(slots);
+    void *dB = nullptr, *dX = nullptr, *dY = nullptr;
+    int st = GBSP_OK;
+    cudaEvent_t ready = nullptr, dense_in = nullptr, all_out = nullptr;
+#define GBSP_CU(x)                                                             \
+    do {                                                                       \
+        if ((x) != cudaSuccess && st == GBSP_OK) st = check_launch("host pipeline"); \
+    } while (0)
+    GBSP_CU(cudaStreamCreateWithFlags(&s_in, cudaStreamNonBlocking));
+    GBSP_CU(cudaStreamCreateWithFlags(&s_run, cudaStreamNonBlocking));
+    GBSP_CU(cudaStreamCreateWithFlags(&s_out, cudaStreamNonBlocking));
+    GBSP_CU(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    GBSP_CU(cudaEventCreateWithFlags(&dense_in, cudaEventDisableTiming));
+    GBSP_CU(cudaEventCreateWithFlags(&all_out, cudaEventDisableTiming));
+    if (st) goto done;
+    // everything starts after the work already queued on the caller's stream
+    GBSP_CU(cudaEventRecord(ready, user));
+    GBSP_CU(cudaStreamWaitEvent(s_in, ready, 0));
+    for (auto &x : sl) {
+        if (scratch_alloc((void **)&x.rowptr, sizeof(int32_t) * (size_t)(max_rows + 1), s_in) ||
+            scratch_alloc((void **)&x.colidx, sizeof(int32_t) * (size_t)std::max<int64_t>(max_nnz, 1), s_in) ||
+            scratch_alloc((void **)&x.vals, sizeof(float) * (size_t)std::max<int64_t>(max_nnz, 1), s_in) ||
+            (do_spmm && scratch_alloc((void **)&x.C, sizeof(float) * (size_t)(max_rows * N), s_in)) ||
+            (do_sddmm && scratch_alloc((void **)&x.out, sizeof(float) * (size_t)std::max<int64_t>(max_nnz, 1), s_in))) {
+            st = GBSP_ERR_OOM;
+            goto done;
+        }
+        GBSP_CU(cudaEventCreateWithFlags(&x.copied, cudaEventDisableTiming));
+        GBSP_CU(cudaEventCreateWithFlags(&x.computed, cudaEventDisableTiming));
+        GBSP_CU(cudaEventCreateWithFlags(&x.drained, cudaEventDisableTiming));
+    }
+    if (do_spmm && scratch_alloc(&dB, sizeof(float) * (size_t)(K * N), s_in)) st = GBSP_ERR_OOM;
+    if (!st && do_sddmm &&
+        (scratch_alloc(&dX, sizeof(float) * (size_t)(M * Kd), s_in) ||
+         scratch_alloc(&dY, sizeof(float) * (size_t)(K * Kd), s_in)))
+        st = GBSP_ERR_OOM;
+    if (st) goto done;
+    if (do_spmm) GBSP_CU(cudaMemcpyAsync(dB, B, sizeof(float) * (size_t)(K * N), cudaMemcpyHostToDevice, s_in));
+    if (do_sddmm) {
+        GBSP_CU(cudaMemcpyAsync(dX, X, sizeof(float) * (size_t)(M * Kd), cudaMemcpyHostToDevice, s_in));
+        GBSP_CU(cudaMemcpyAsync(dY, Y, sizeof(float) * (size_t)(K * Kd), cudaMemcpyHostToDevice, s_in));
+    }
+    GBSP_CU(cudaEventRecord(dense_in, s_in));
+    GBSP_CU(cudaStreamWaitEvent(s_run, dense_in, 0));
+    for (int c = 0; c < chunks && !st; ++c) {
+        Slot &x = sl[c % slots];
+        const int64_t r0 = bounds[c], r1 = bounds[c + 1], mr = r1 - r0;
+        const int64_t p0 = rowptr[r0], p1 = rowptr[r1], ne = p1 - p0;
+        if (c >= slots) GBSP_CU(cudaStreamWaitEvent(s_in, x.drained, 0));  // slot's previous results are out
+        GBSP_CU(cudaMemcpyAsync(x.rowptr, rowptr + r0, sizeof(int32_t) * (size_t)(mr + 1), cudaMemcpyHostToDevice, s_in));
+        if (ne > 0) {
+            GBSP_CU(cudaMemcpyAsync(x.colidx, colidx + p0, sizeof(int32_t) * (size_t)ne, cudaMemcpyHostToDevice, s_in));
+            GBSP_CU(cudaMemcpyAsync(x.vals, vals + p0, sizeof(float) * (size_t)ne, cudaMemcpyHostToDevice, s_in));
+        }
+        GBSP_CU(cudaEventRecord(x.copied, s_in));
+        GBSP_CU(cudaStreamWaitEvent(s_run, x.copied, 0));
+        if (do_spmm) {
+            SpmmProblem p{};
+            p.M = (int32_t)mr;
+            p.K = (int32_t)K;
+            p.N = (int32_t)N;
+            p.nnz = ne;
+            p.rowptr = x.rowptr;
+            p.colidx = x.colidx - p0;  // absolute entry numbers index the chunk buffer
+            p.vals = x.vals - p0;
+            p.B = dB;
+            p.ldb = N;
+            p.C = x.C;
+            p.ldc = N;
+            p.dtype = GBSP_F32;
+            if ((st = launch_spmm(p, GBSP_VARIANT_ROWSPLIT, 0, 0, 0, s_run))) break;
+        }
+        if (do_sddmm && ne > 0) {
+            SddmmProblem q{};
+            q.M = (int32_t)mr;
+            q.N = (int32_t)K;
+            q.Kd = (int32_t)Kd;
+            q.nnz = ne;
+            q.rowptr = x.rowptr;
+            q.colidx = x.colidx - p0;
+            q.svals = x.vals - p0;
+            q.X = static_cast<const float *>(dX) + r0 * Kd;
+            q.ldx = Kd;
+            q.Y = dY;
+            q.ldy = Kd;
+            q.out = x.out - p0;
+            q.dtype = GBSP_F32;
+            if ((st = launch_sddmm(q, Kd <= 512 ? GBSP_VARIANT_ROWSPLIT : GBSP_VARIANT_SCALAR, 0, s_run))) break;
+        }
+        GBSP_CU(cudaEventRecord(x.computed, s_run));
+        GBSP_CU(cudaStreamWaitEvent(s_out, x.computed, 0));
+        if (do_spmm)
+            GBSP_CU(cudaMemcpyAsync(C + r0 * N, x.C, sizeof(float) * (size_t)(mr * N), cudaMemcpyDeviceToHost, s_out));
+        if (do_sddmm && ne > 0)
+            GBSP_CU(cudaMemcpyAsync(out + p0, x.out, sizeof(float) * (size_t)ne, cudaMemcpyDeviceToHost, s_out));
+        GBSP_CU(cudaEventRecord(x.drained, s_out));
+    }
+    // the caller's stream resumes after every result is on the host
+    GBSP_CU(cudaEventRecord(all_out, s_out));
+    GBSP_CU(cudaStreamWaitEvent(user, all_out, 0));
+done:
+#undef GBSP_CU
+    for (auto &x : sl) {
+        scratch_free(x.rowptr, s_out);
+        scratch_free(x.colidx, s_out);
+        scratch_free(x.vals, s_out);
+        scratch_free(x.C, s_out);
+        scratch_free(x.out, s_out);
+        if (x.copied) cudaEventDestroy(x.copied);
+        if (x.computed) cudaEventDestroy(x.computed);
+        if (x.drained) cudaEventDestroy(x.drained);
+    }
+    scratch_free(dB, s_out);
+    scratch_free(dX, s_out);
+    scratch_free(dY, s_out);
+    if (ready) cudaEventDestroy(ready);
+    if (dense_in) cudaEventDestroy(dense_in);
+    if (all_out) cudaEventDestroy(all_out);
+    if (s_in) cudaStreamDestroy(s_in);
+    if (s_run) cudaStreamDestroy(s_run);
+    if (s_out) cudaStreamDestroy(s_out);
+    return st ? st : ok();
+}

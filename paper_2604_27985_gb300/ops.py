@@ -243,3 +243,81 @@ def gnn_sddmm_spmm_batched(graphs, stream=None) -> None:
     """One-shot batched chain (creates, runs and destroys a plan; synchronises)."""
     G, S, Hd, E, Od = _gnn_arrays(graphs)
     check(lib.gnn_sddmm_spmm_batched(G, S, Hd, E, Od, _stream(stream)))
+
+
+# ---- kernel selection ------------------------------------------------------------------------
+
+N_VARIANTS = 24
+N_FEATURES = 16
+N_PARAMS = 16 * 64 + 64 + 64 * 64 + 64 + 24 * 64 + 24
+
+
+def variant_options(v: int) -> dict:
+    """spmm keyword arguments of selector variant v (gbsp_variant_opts)."""
+    o = Opts()
+    check(lib.gbsp_variant_opts(int(v), ctypes.byref(o)))
+    name = {1: "rowsplit", 2: "merge", 3: "scalar"}[o.variant]
+    return {"variant": name, "vecs": o.vecs, "unroll": o.unroll, "ctas_per_sm": o.ctas_per_sm}
+
+
+def features(rowptr, colidx, ncols, N, dtype=F32, out=None, stream=None) -> torch.Tensor:
+    """The 16 selector features of a CSR matrix (device float32[16])."""
+    if out is None:
+        out = torch.empty(N_FEATURES, dtype=torch.float32, device=rowptr.device)
+    A = Csr(rowptr.numel() - 1, int(ncols), colidx.numel(), _ptr(rowptr), _ptr(colidx), _ptr(colidx), None, F32)
+    check(lib.gbsp_features(ctypes.byref(A), int(N), int(dtype), _ptr(out), _stream(stream)))
+    return out
+
+
+def feature_norm(feats: torch.Tensor, stream=None) -> torch.Tensor:
+    norm = torch.empty(2 * N_FEATURES, dtype=torch.float32, device=feats.device)
+    check(lib.gbsp_feature_norm(_ptr(feats), feats.shape[0], _ptr(norm), _stream(stream)))
+    return norm
+
+
+def mlp_predict(weights, norm, feats, stream=None):
+    n = feats.shape[0]
+    out = torch.empty((n, N_VARIANTS), dtype=torch.float32, device=feats.device)
+    choice = torch.empty(n, dtype=torch.int32, device=feats.device)
+    check(lib.gbsp_mlp_predict(_ptr(weights), _ptr(norm), _ptr(feats), n, _ptr(out), _ptr(choice), _stream(stream)))
+    return out, choice
+
+
+def mlp_train(weights, adam, norm, feats, targets, mask, order, steps, batch=64, lr=1e-3, t0=0, stream=None):
+    check(lib.gbsp_mlp_train(_ptr(weights), _ptr(adam), _ptr(norm), _ptr(feats), _ptr(targets), _ptr(mask),
+                             _ptr(order), order.numel(), int(steps), int(batch), float(lr), int(t0), _stream(stream)))
+
+
+def autotune(rowptr, colidx, vals, B, C, reps=3, a_scale=None, b_scale=None, stream=None):
+    """Times of the 24 variants (ms, inf where not applicable) and the best index."""
+    A = _csr(rowptr, colidx, vals, B.shape[0], a_scale)
+    b, c = _dense(B, b_scale), _dense(C)
+    times = (ctypes.c_float * N_VARIANTS)()
+    best = ctypes.c_int32(-1)
+    check(lib.gbsp_autotune(ctypes.byref(A), ctypes.byref(b), ctypes.byref(c), int(reps), times, ctypes.byref(best),
+                            _stream(stream)))
+    return [times[i] for i in range(N_VARIANTS)], best.value
+
+
+def _hptr(a):
+    """Host address of a CPU tensor or numpy array (None for None)."""
+    if a is None:
+        return None
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda:
+            raise ValueError("host pipeline operands live in host memory")
+        return a.data_ptr() or None
+    return a.ctypes.data or None
+
+
+def spmm_sddmm_host(rowptr, colidx, vals, B=None, C=None, X=None, Y=None, out=None, ncols=None, chunks=8, slots=2,
+                    stream=None) -> None:
+    """SpMM and / or SDDMM on host-resident FP32 operands, streamed through the device in
+    row chunks (gbsp_spmm_sddmm_host).  Synchronise the stream before reading C / out."""
+    M = rowptr.shape[0] - 1
+    nnz = colidx.shape[0]
+    K = int(ncols if ncols is not None else (B.shape[0] if B is not None else Y.shape[0]))
+    N = B.shape[1] if B is not None else 0
+    Kd = X.shape[1] if X is not None else 0
+    check(lib.gbsp_spmm_sddmm_host(_hptr(rowptr), _hptr(colidx), _hptr(vals), _hptr(B), _hptr(C), N, _hptr(X),
+                                   _hptr(Y), _hptr(out), Kd, M, K, nnz, int(chunks), int(slots), _stream(stream)))
