@@ -5,8 +5,8 @@
 // accumulation, BF16 O_g (round to nearest even).
 //
 // One persistent launch covers the whole batch: the work list holds tiles of consecutive
-// rows of one graph with about the same number of edges; warps take tiles from an atomic
-// ticket.  Each row is fused: every gathered H_j serves both the dot product with H_i (its
+// rows (at most 63) of one graph with about the same number of edges; warps take tiles from
+// an atomic ticket.  Each row is fused: every gathered H_j serves both the dot product with H_i (its
 // edge's E value, reduced across the lane group by an xor butterfly) and the accumulation
 // E_ij * H_j into O_i, so H_j is read once per edge.  The launch (and the ticket reset) is
 // recorded once into a CUDA graph and replayed per execution.
@@ -40,103 +40,110 @@ struct GnnArgs {
     unsigned *ticket;
 };
 
-// One row of one graph with LPN lanes x VPL BF16 vectors (8 features each) per edge.
-template <int LPN, int VPL, int U>
-__device__ __forceinline__ void gnn_row(const GraphDesc &g, int row, int lane) {
+// The rows [r0, r1) (at most 63) of one graph, one after another, with LPN lanes per edge
+// and one 16-byte BF16 vector (8 features) per lane.  The tile's row pointers sit in two
+// registers per lane; the next row's first 32 column indices and values and its H row are
+// loaded while the current row computes, so a row starts with its data in registers.
+template <int LPN, int U>
+__device__ __forceinline__ void gnn_tile(const GraphDesc &g, int r0, int r1, int lane) {
     constexpr int G = 32 / LPN;
     constexpr int STEP = G * U;
     static_assert(STEP <= 32 && 32 % STEP == 0, "whole steps per chunk");
     const int sl = lane % LPN, sub = lane / LPN;
-    bool colok[VPL];
-    float x[VPL][8];
+    const bool colok = sl * 8 < g.N;
     const uint4 *Hv = reinterpret_cast<const uint4 *>(g.H) + sl;
     const int64_t ldv = g.ldh / 8;
-#pragma unroll
-    for (int v = 0; v < VPL; ++v) {
-        colok[v] = (v * LPN + sl) * 8 < g.N;
-        uint4 raw = make_uint4(0, 0, 0, 0);
-        if (colok[v]) raw = __ldg(Hv + (int64_t)row * ldv + v * LPN);
-        BF16::unpack(raw, x[v]);
-    }
-    float acc[VPL][8];
-#pragma unroll
-    for (int v = 0; v < VPL; ++v)
-#pragma unroll
-        for (int k = 0; k < 8; ++k) acc[v][k] = 0.f;
-
-    const int64_t p0 = g.rowptr[row], p1 = g.rowptr[row + 1];
+    const int nrows = r1 - r0;
+    const int rp_a = lane <= nrows ? g.rowptr[r0 + lane] : 0;
+    const int rp_b = lane + 32 <= nrows ? g.rowptr[r0 + 32 + lane] : 0;
+    auto start = [&](int k) {
+        const int a = __shfl_sync(FULL, rp_a, k & 31), b = __shfl_sync(FULL, rp_b, k & 31);
+        return k < 32 ? a : b;
+    };
+    int64_t p0 = start(0), p1 = start(1);
     int c = 0;
     float s = 0.f;
     if (p0 + lane < p1) {
         c = ld_stream(g.colidx + p0 + lane);
         s = ld_stream(g.svals + p0 + lane);
     }
-    for (int64_t base = p0; base < p1; base += 32) {
-        const int64_t nb = base + 32;
-        int c2 = 0;
-        float s2 = 0.f;
-        if (nb + lane < p1) {
-            c2 = ld_stream(g.colidx + nb + lane);
-            s2 = ld_stream(g.svals + nb + lane);
-        }
-        const int cnt = (int)min((int64_t)32, p1 - base);
-#pragma unroll 1
-        for (int q = 0; q < cnt; q += STEP) {
-            uint4 raw[U][VPL];
-            float sj[U];
-            bool ok[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int idx = q + u * G + sub;
-                const int cj = __shfl_sync(FULL, c, idx);
-                sj[u] = __shfl_sync(FULL, s, idx);
-                ok[u] = idx < cnt;
-                const uint4 *rp = Hv + (int64_t)cj * ldv;
-#pragma unroll
-                for (int v = 0; v < VPL; ++v)
-                    raw[u][v] = (ok[u] && colok[v]) ? __ldg(rp + v * LPN) : make_uint4(0, 0, 0, 0);
+    uint4 xraw = colok ? __ldg(Hv + (int64_t)r0 * ldv) : make_uint4(0, 0, 0, 0);
+    for (int k = 0; k < nrows; ++k) {
+        const int row = r0 + k;
+        // next row, loaded now
+        int64_t q1 = p1;
+        int cn = 0;
+        float sn = 0.f;
+        uint4 xn = make_uint4(0, 0, 0, 0);
+        if (k + 1 < nrows) {
+            q1 = start(k + 2);
+            if (p1 + lane < q1) {
+                cn = ld_stream(g.colidx + p1 + lane);
+                sn = ld_stream(g.svals + p1 + lane);
             }
+            if (colok) xn = __ldg(Hv + (int64_t)(row + 1) * ldv);
+        }
+        float x[8], acc[8];
+        BF16::unpack(xraw, x);
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                float f[VPL][8];
-                float dot = 0.f;
+        for (int t = 0; t < 8; ++t) acc[t] = 0.f;
+        for (int64_t base = p0; base < p1; base += 32) {
+            if (base > p0) {  // rows longer than 32 edges load their later chunks here
+                c = 0;
+                s = 0.f;
+                if (base + lane < p1) {
+                    c = ld_stream(g.colidx + base + lane);
+                    s = ld_stream(g.svals + base + lane);
+                }
+            }
+            const int cnt = (int)min((int64_t)32, p1 - base);
+#pragma unroll 1
+            for (int q = 0; q < cnt; q += STEP) {
+                uint4 raw[U];
+                float sj[U];
+                bool ok[U];
 #pragma unroll
-                for (int v = 0; v < VPL; ++v) {
-                    BF16::unpack(raw[u][v], f[v]);
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) dot = fmaf(x[v][k], f[v][k], dot);
+                for (int u = 0; u < U; ++u) {
+                    const int idx = q + u * G + sub;
+                    const int cj = __shfl_sync(FULL, c, idx);
+                    sj[u] = __shfl_sync(FULL, s, idx);
+                    ok[u] = idx < cnt;
+                    raw[u] = (ok[u] && colok) ? __ldg(Hv + (int64_t)cj * ldv) : make_uint4(0, 0, 0, 0);
                 }
 #pragma unroll
-                for (int off = LPN / 2; off >= 1; off >>= 1) dot += __shfl_xor_sync(FULL, dot, off);
-                const float e = sj[u] * dot;
-                if (sl == 0 && ok[u]) g.E[base + q + u * G + sub] = e;
+                for (int u = 0; u < U; ++u) {
+                    float f[8];
+                    BF16::unpack(raw[u], f);
+                    float dot = 0.f;
 #pragma unroll
-                for (int v = 0; v < VPL; ++v)
+                    for (int t = 0; t < 8; ++t) dot = fmaf(x[t], f[t], dot);
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) acc[v][k] = fmaf(e, f[v][k], acc[v][k]);
+                    for (int off = LPN / 2; off >= 1; off >>= 1) dot += __shfl_xor_sync(FULL, dot, off);
+                    const float e = sj[u] * dot;
+                    if (sl == 0 && ok[u]) g.E[base + q + u * G + sub] = e;
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) acc[t] = fmaf(e, f[t], acc[t]);
+                }
             }
         }
-        c = c2;
-        s = s2;
-    }
 #pragma unroll
-    for (int off = LPN; off < 32; off <<= 1)
+        for (int off = LPN; off < 32; off <<= 1)
 #pragma unroll
-        for (int v = 0; v < VPL; ++v)
-#pragma unroll
-            for (int k = 0; k < 8; ++k) acc[v][k] += __shfl_xor_sync(FULL, acc[v][k], off);
-    if (lane < LPN) {
-#pragma unroll
-        for (int v = 0; v < VPL; ++v) {
-            if (!colok[v]) continue;
+            for (int t = 0; t < 8; ++t) acc[t] += __shfl_xor_sync(FULL, acc[t], off);
+        if (lane < LPN && colok) {
             uint32_t w[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                __nv_bfloat162 h = __floats2bfloat162_rn(acc[v][2 * k], acc[v][2 * k + 1]);
-                w[k] = *reinterpret_cast<uint32_t *>(&h);
+            for (int t = 0; t < 4; ++t) {
+                __nv_bfloat162 h = __floats2bfloat162_rn(acc[2 * t], acc[2 * t + 1]);
+                w[t] = *reinterpret_cast<uint32_t *>(&h);
             }
-            reinterpret_cast<uint4 *>(g.O + (int64_t)row * g.ldo)[v * LPN + sl] = make_uint4(w[0], w[1], w[2], w[3]);
+            reinterpret_cast<uint4 *>(g.O + (int64_t)row * g.ldo)[sl] = make_uint4(w[0], w[1], w[2], w[3]);
         }
+        p0 = p1;
+        p1 = q1;
+        c = cn;
+        s = sn;
+        xraw = xn;
     }
 }
 
@@ -149,14 +156,12 @@ __global__ void __launch_bounds__(256) gnn_kernel(const GnnArgs a) {
         if (t >= (unsigned)a.ntiles) return;
         const Tile tile = a.tiles[t];
         const GraphDesc g = a.graphs[tile.graph];
-        for (int row = tile.row0; row < tile.row1; ++row) {
-            if (g.N <= 64)
-                gnn_row<8, 1, 4>(g, row, lane);
-            else if (g.N <= 128)
-                gnn_row<8, 2, 2>(g, row, lane);
-            else
-                gnn_row<16, 2, 2>(g, row, lane);
-        }
+        if (g.N <= 64)
+            gnn_tile<8, 4>(g, tile.row0, tile.row1, lane);
+        else if (g.N <= 128)
+            gnn_tile<16, 2>(g, tile.row0, tile.row1, lane);
+        else
+            gnn_tile<32, 2>(g, tile.row0, tile.row1, lane);
     }
 }
 
@@ -230,7 +235,7 @@ GBSP_EXPORT int gbsp_gnn_plan_create(int G, const gbsp_csr *S, const gbsp_dense 
         int32_t r0 = 0;
         while (r0 < a.rows) {
             int32_t r1 = r0 + 1;
-            while (r1 < a.rows && rp[r1 + 1] - rp[r0] <= edges_per_tile && r1 - r0 < 64) ++r1;
+            while (r1 < a.rows && rp[r1 + 1] - rp[r0] <= edges_per_tile && r1 - r0 < 63) ++r1;
             tiles.push_back(Tile{g, r0, r1});
             r0 = r1;
         }

@@ -34,6 +34,7 @@ constexpr int kKCH = 64;       // condensed columns per pipeline stage
 constexpr int kBlkPerCh = kKCH / kBC;
 constexpr int kATile = kBR * kKCH * 2;  // bytes of one stage of window values
 constexpr uint64_t kWaitNs = 1000000000ull;  // a bounded wait gives up after one second
+constexpr int kStagedCols = 1024;  // block columns of a window staged in shared memory
 
 // ---- PTX wrappers ---------------------------------------------------------------------------
 
@@ -79,6 +80,16 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
             smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// One box of a 3-D view of B: (64 features, rows, feature atoms) with the atoms outermost,
+// so one copy lands a dense block's 8 rows as NFA consecutive 1 KB MN-major atoms.
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
 }
 
@@ -150,7 +161,8 @@ struct TcArgs {
     float *C;
     int64_t ldc;
     int M, K, N;
-    int *err;  // set on a timed-out wait
+    int *err;       // set on a timed-out wait
+    int block_box;  // 1: the tensor map is the 3-D atom view (one copy per block); 0: 2-D
 };
 
 template <int NT>
@@ -158,13 +170,13 @@ struct TcShape {
     static constexpr int NFA = 2 * NT;                      // 64-feature atoms per k-row group
     static constexpr int BT = kKCH * NT * 128 * 2;          // gathered B bytes per stage
     static constexpr int STAGE = BT + kATile;               // bytes per stage
-    static constexpr int S = NT <= 2 ? 4 : (NT == 3 ? 3 : 2);  // pipeline depth
+    static constexpr int S = NT <= 2 ? 3 : 2;                  // pipeline depth (2 CTAs per SM for NT <= 2)
     static constexpr int NCOLS = NT <= 2 ? 32 : 64;         // TMEM columns (16 per feature tile)
     static constexpr int SMEM = S * STAGE + 1024 + 256;     // + alignment slack + barriers
 };
 
 template <int NT>
-__global__ void __launch_bounds__(128, 1) tc_window_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
+__global__ void __launch_bounds__(128) tc_window_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     using SH = TcShape<NT>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -173,11 +185,15 @@ __global__ void __launch_bounds__(128, 1) tc_window_kernel(const __grid_constant
     uint64_t *done = empty + SH::S;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
 
+    __shared__ int32_t s_cols[kStagedCols];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int w = blockIdx.x;
     const int b0 = a.win_blk[w], b1 = a.win_blk[w + 1];
     const int nch = (b1 - b0) / kBlkPerCh;
     const int row0 = a.win_row0[w];
+    // the producer reads each block's column from shared memory, not from a dependent
+    // global load per TMA
+    for (int i = threadIdx.x; i < b1 - b0 && i < kStagedCols; i += blockDim.x) s_cols[i] = a.blk_col[b0 + i];
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < SH::S; ++s) {
@@ -201,10 +217,16 @@ __global__ void __launch_bounds__(128, 1) tc_window_kernel(const __grid_constant
             bulk_load(bt + SH::BT, a.atiles + (size_t)(b0 / kBlkPerCh + ch) * kATile, kATile, &full[s]);
 #pragma unroll 1
             for (int kb = 0; kb < kBlkPerCh; ++kb) {
-                const int col = a.blk_col[b0 + ch * kBlkPerCh + kb];
+                const int q = ch * kBlkPerCh + kb;
+                const int col = q < kStagedCols ? s_cols[q] : a.blk_col[b0 + q];
                 const int y = col >= 0 ? col * kBC : a.K;  // padding block: rows past K read as zeros
+                if (a.block_box) {
+                    tma_load_3d(bt + kb * SH::NFA * 1024, &tmB, &full[s], 0, y, 0);
+                } else {
 #pragma unroll
-                for (int fa = 0; fa < SH::NFA; ++fa) tma_load_2d(bt + (kb * SH::NFA + fa) * 1024, &tmB, &full[s], 64 * fa, y);
+                    for (int fa = 0; fa < SH::NFA; ++fa)
+                        tma_load_2d(bt + (kb * SH::NFA + fa) * 1024, &tmB, &full[s], 64 * fa, y);
+                }
             }
         };
         bool ok = true;
@@ -632,18 +654,32 @@ GBSP_EXPORT int gbsp_plan_execute(const gbsp_plan *p, const gbsp_dense *B, gbsp_
     if (p->nwin_tc == 0 || N == 0) return ok();
     EncodeTiledFn enc = encode_fn();
     if (!enc) return fail(GBSP_ERR_CUDA, "plan execute: cuTensorMapEncodeTiled is not available");
-    CUtensorMap map;
-    const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)p->K};
-    const cuuint64_t strides[1] = {(cuuint64_t)B->ld * 2};
-    const cuuint32_t box[2] = {64, 8};
-    const cuuint32_t estr[2] = {1, 1};
-    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, B->data, dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return fail(GBSP_ERR_CUDA, "plan execute: tensor map encoding failed");
-    TcArgs args{p->tc_row0, p->tc_blk, p->blk_col, p->atiles, static_cast<float *>(C->data), C->ld, (int)p->M,
-                (int)p->K, (int)N, p->err};
     const int nt = (int)((N + 127) / 128);
+    CUtensorMap map;
+    int block_box = 0;
+    if (N % 128 == 0) {
+        // 3-D view: (64 features, K rows, N / 64 atoms), atoms 128 B apart, rows ld apart
+        const cuuint64_t dims3[3] = {64, (cuuint64_t)p->K, (cuuint64_t)(N / 64)};
+        const cuuint64_t strides3[2] = {(cuuint64_t)B->ld * 2, 128};
+        const cuuint32_t box3[3] = {64, 8, (cuuint32_t)(2 * nt)};
+        const cuuint32_t estr3[3] = {1, 1, 1};
+        block_box = 2 * nt == (int)(N / 64) &&
+                    enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, B->data, dims3, strides3, box3, estr3,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    if (!block_box) {
+        const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)p->K};
+        const cuuint64_t strides[1] = {(cuuint64_t)B->ld * 2};
+        const cuuint32_t box[2] = {64, 8};
+        const cuuint32_t estr[2] = {1, 1};
+        if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, B->data, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return fail(GBSP_ERR_CUDA, "plan execute: tensor map encoding failed");
+    }
+    TcArgs args{p->tc_row0, p->tc_blk, p->blk_col, p->atiles, static_cast<float *>(C->data), C->ld, (int)p->M,
+                (int)p->K, (int)N, p->err, block_box};
     switch (nt) {
         case 1: st = launch_tc<1>(map, args, p->nwin_tc, s); break;
         case 2: st = launch_tc<2>(map, args, p->nwin_tc, s); break;
