@@ -189,7 +189,7 @@ void gbsp_plan_destroy(gbsp_plan *plan);
  * S_g: square FP32 CSR with nnz given; H_g, O_g: BF16 n_g x N_g (N_g a multiple of 8,
  * at most 256, rows 16-byte aligned); E[g]: device float[nnz_g] in CSR order.  Accumulation
  * is FP32; O is rounded to BF16 (nearest even).  The plan builds a device work list of row
- * tiles (about edges_per_tile edges each, default 2048 when <= 0) over all graphs and
+ * tiles (about edges_per_tile edges each, default 512 when <= 0) over all graphs and
  * records one persistent launch, which takes tiles from an atomic ticket, into a CUDA
  * graph; gbsp_gnn_plan_execute replays it on the stream (asynchronous).  The plan keeps the
  * caller's pointers: the data may change between executions, the allocations may not.

@@ -5,8 +5,9 @@
 // accumulation, BF16 O_g (round to nearest even).
 //
 // One persistent launch covers the whole batch: the work list holds tiles of consecutive
-// rows (at most 63) of one graph with about the same number of edges; warps take tiles from
-// an atomic ticket.  Each row is fused: every gathered H_j serves both the dot product with H_i (its
+// rows (at most 63) of one graph with about the same number of edges (512 by default, so
+// the tiles in flight at once span few graphs and their features stay in L2); warps take
+// tiles from an atomic ticket in graph order.  Each row is fused: every gathered H_j serves both the dot product with H_i (its
 // edge's E value, reduced across the lane group by an xor butterfly) and the accumulation
 // E_ij * H_j into O_i, so H_j is read once per edge.  The launch (and the ticket reset) is
 // recorded once into a CUDA graph and replayed per execution.
@@ -202,7 +203,7 @@ GBSP_EXPORT int gbsp_gnn_plan_create(int G, const gbsp_csr *S, const gbsp_dense 
     if (!out) return fail(GBSP_ERR_INVALID_ARG, "gnn plan: null output");
     *out = nullptr;
     if (G < 0 || (G > 0 && (!S || !H || !E || !O))) return fail(GBSP_ERR_INVALID_ARG, "gnn plan: bad arrays");
-    if (edges_per_tile <= 0) edges_per_tile = 2048;
+    if (edges_per_tile <= 0) edges_per_tile = 512;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     std::vector<GraphDesc> graphs(G);
     std::vector<Tile> tiles;

@@ -210,8 +210,16 @@ __global__ void __launch_bounds__(128) tc_window_kernel(const __grid_constant__ 
     fence_after_sync();
     const uint32_t taddr = *tslot;
 
+    // warp 0 produces (TMA), warp 1 issues the MMAs; each runs ahead as far as the stages allow
     if (threadIdx.x == 0) {
-        auto issue = [&](int s, int ch) {
+        bool ok = true;
+        int issued = 0;
+        for (int ch = 0; ch < nch; ++ch) {
+            const int s = ch % SH::S;
+            if (ch >= SH::S && !mbar_wait(&empty[s], ((ch / SH::S) - 1) & 1)) {  // stage's MMAs done
+                ok = false;
+                break;
+            }
             uint8_t *bt = smem + s * SH::STAGE;
             mbar_expect_tx(&full[s], SH::STAGE);
             bulk_load(bt + SH::BT, a.atiles + (size_t)(b0 / kBlkPerCh + ch) * kATile, kATile, &full[s]);
@@ -228,18 +236,20 @@ __global__ void __launch_bounds__(128) tc_window_kernel(const __grid_constant__ 
                         tma_load_2d(bt + (kb * SH::NFA + fa) * 1024, &tmB, &full[s], 64 * fa, y);
                 }
             }
-        };
+            issued = ch + 1;
+        }
+        if (!ok) atomicExch(a.err, 1);
+        // every issued copy lands before the CTA can leave (bounded waits)
+        for (int ch = issued - SH::S > 0 ? issued - SH::S : 0; ch < issued; ++ch)
+            mbar_wait(&full[ch % SH::S], (ch / SH::S) & 1);
+    } else if (threadIdx.x == 32) {
         bool ok = true;
-        const int pro = nch < SH::S ? nch : SH::S;
-        for (int s = 0; s < pro; ++s) issue(s, s);
-        int issued = pro, consumed = 0;
         for (int i = 0; i < nch; ++i) {
             const int s = i % SH::S;
             if (!mbar_wait(&full[s], (i / SH::S) & 1)) {
                 ok = false;
                 break;
             }
-            consumed = i + 1;
             fence_after_sync();
             const uint32_t bt = smem_u32(smem + s * SH::STAGE);
             const uint32_t at = bt + SH::BT;
@@ -253,23 +263,9 @@ __global__ void __launch_bounds__(128) tc_window_kernel(const __grid_constant__ 
                 }
             }
             mma_commit(&empty[s]);
-            // refill the stage of the previous chunk once its MMAs have finished
-            if (i >= 1 && i - 1 + SH::S < nch) {
-                const int sp = (i - 1) % SH::S;
-                if (!mbar_wait(&empty[sp], ((i - 1) / SH::S) & 1)) {
-                    ok = false;
-                    break;
-                }
-                issue(sp, i - 1 + SH::S);
-                ++issued;
-            }
         }
         mma_commit(done);
-        if (!ok) {
-            atomicExch(a.err, 1);
-            // let the copies already issued land (each wait is bounded) before the CTA exits
-            for (int i = consumed; i < issued; ++i) mbar_wait(&full[i % SH::S], (i / SH::S) & 1);
-        }
+        if (!ok) atomicExch(a.err, 1);
     }
     __syncwarp();
     const bool have = mbar_wait(done, 0);
