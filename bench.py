@@ -154,6 +154,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of per-rank timings over the process group (the slowest rank
+    sets the job's time)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_gflops(world, gflop_per_rank, ms_max):
+    """Replicas: every rank does the same work, the job takes the slowest rank's time."""
+    return world * gflop_per_rank / (ms_max / 1e3)
+
+
 def kernel_traffic():
     """Per-launch DRAM bytes of the SpMM kernel from the committed ncu summary, or None
     if the kernel sources changed since those counters were taken."""
@@ -299,11 +315,9 @@ def run_ours(args):
 
     ms = total_ms / args.steps
     if world > 1:
-        tt = torch.tensor([ms, e2e_ms, spmm_ms, sddmm_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms, e2e_ms, spmm_ms, sddmm_ms = tt.tolist()
+        ms, e2e_ms, spmm_ms, sddmm_ms = max_over_ranks([ms, e2e_ms, spmm_ms, sddmm_ms], dev)
     gflop = flops(nnz) / 1e9
-    value = world * gflop / (ms / 1e3)
+    value = whole_job_gflops(world, gflop, ms)
     peak, peak_kind = peaks()
     spmm_bytes = gather_bytes_spmm(nnz, M, N_SPMM)
     sddmm_bytes = gather_bytes_sddmm(nnz, M, KD_SDDMM)

@@ -170,7 +170,7 @@ int gbsp_spmm_sddmm_host(const int32_t *rowptr, const int32_t *colidx, const flo
  * residual_opts (may be NULL) chooses the residual kernel.  gbsp_plan_create synchronises
  * the stream; gbsp_plan_execute is asynchronous and may be repeated with new B and C.
  * Device-side waits in the tensor-core kernel give up after about a second and record it;
- * gbsp_plan_check (synchronous) returns GBSP_ERR_TIMEOUT if any did.
+ * gbsp_plan_check (synchronous) returns GBSP_ERR_TIMEOUT if any did since the last check.
  * gbsp_plan_info fills info[0..4] = {dense windows, dense blocks (padded to multiples of 8
  * per window), entries inside dense blocks, residual entries, threshold}. */
 typedef struct gbsp_plan gbsp_plan;
@@ -179,6 +179,11 @@ int gbsp_plan_create(const gbsp_csr *A, int32_t threshold, const gbsp_opts *resi
 int gbsp_plan_execute(const gbsp_plan *plan, const gbsp_dense *B, gbsp_dense *C, void *stream);
 int gbsp_plan_info(const gbsp_plan *plan, int64_t *info, int n);
 int gbsp_plan_check(const gbsp_plan *plan, void *stream);
+/* Testing the timeout path (no counterpart in the paper): while chunk >= 0, the first
+ * dense window's kernel never loads that stage, so its MMA warp's wait runs out after about
+ * a second, the kernel records it and returns; gbsp_plan_check then reports
+ * GBSP_ERR_TIMEOUT (once) and the context stays usable.  chunk = -1 switches it off. */
+int gbsp_plan_test_withhold(gbsp_plan *plan, int32_t chunk);
 void gbsp_plan_destroy(gbsp_plan *plan);
 
 /* ---- batched graph chain (one persistent launch in a CUDA graph) ---------------------------- */

@@ -68,6 +68,7 @@ def _load() -> ctypes.CDLL:
         "gbsp_plan_execute": [P, ctypes.POINTER(Dense), ctypes.POINTER(Dense), P],
         "gbsp_plan_info": [P, ctypes.POINTER(I64), I],
         "gbsp_plan_check": [P, P],
+        "gbsp_plan_test_withhold": [P, ctypes.c_int32],
         "gbsp_gnn_plan_create": [I, ctypes.POINTER(Csr), ctypes.POINTER(Dense), ctypes.POINTER(P),
                                  ctypes.POINTER(Dense), ctypes.c_int32, P, ctypes.POINTER(P)],
         "gbsp_gnn_plan_execute": [P, P],

@@ -1,6 +1,8 @@
 // C ABI entry points: argument checks, variant choice and dispatch to the kernels.
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
 
 #include <atomic>
 #include <mutex>
@@ -35,6 +37,21 @@ int ok() {
 
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+// Host-side fault injection for testing the error paths without touching the GPU:
+// GBSP_FAULT=alloc makes workspace allocation fail, =launch makes the SpMM / SDDMM entry
+// points fail before launching, =validate makes gbsp_csr_validate report a bad matrix.
+int injected_fault() {
+    static int f = [] {
+        const char *e = getenv("GBSP_FAULT");
+        if (!e) return 0;
+        if (!strcmp(e, "alloc")) return 1;
+        if (!strcmp(e, "launch")) return 2;
+        if (!strcmp(e, "validate")) return 3;
+        return 0;
+    }();
+    return f;
+}
+
 int check_launch(const char *what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(GBSP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
@@ -53,6 +70,10 @@ int sm_count() {
 }
 
 int scratch_alloc(void **ptr, size_t bytes, cudaStream_t s) {
+    if (injected_fault() == 1) {
+        *ptr = nullptr;
+        return fail(GBSP_ERR_OOM, "injected workspace allocation failure (GBSP_FAULT=alloc)");
+    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return fail(GBSP_ERR_CUDA, "no current device");
     {
@@ -154,6 +175,7 @@ GBSP_EXPORT int spmm_csr_ex(const gbsp_csr *A, const gbsp_dense *B, gbsp_dense *
         if ((st = gbsp_csr_validate(A, stream, &bad))) return st;
     }
     if (A->rows == 0 || B->cols == 0) return ok();
+    if (injected_fault() == 2) return fail(GBSP_ERR_CUDA, "spmm: injected launch failure (GBSP_FAULT=launch)");
     const bool vec = vec_ok(B) && aligned16(C->data) && C->ld % 4 == 0;
     int variant = o.variant;
     if (variant == GBSP_VARIANT_AUTO) variant = vec ? GBSP_VARIANT_ROWSPLIT : GBSP_VARIANT_SCALAR;
@@ -202,6 +224,7 @@ GBSP_EXPORT int sddmm_csr_ex(const gbsp_csr *S, const gbsp_dense *X, const gbsp_
         if ((st = gbsp_csr_validate(S, stream, &bad))) return st;
     }
     if (S->rows == 0 || S->nnz == 0) return ok();
+    if (injected_fault() == 2) return fail(GBSP_ERR_CUDA, "sddmm: injected launch failure (GBSP_FAULT=launch)");
     const int V = elems_per_vec(X->dtype);
     const bool vec = vec_ok(X) && vec_ok(Y) && X->cols > 0 && X->cols <= 32 * 16;
     int variant = o.variant;
@@ -254,6 +277,10 @@ GBSP_EXPORT int gbsp_csr_validate(const gbsp_csr *A, void *stream, int64_t *n_ba
     if ((st = check_csr(A, "validate"))) return st;
     if (!n_bad) return fail(GBSP_ERR_INVALID_ARG, "validate: null n_bad");
     if (A->nnz < 0) return fail(GBSP_ERR_INVALID_ARG, "validate: nnz must be given");
+    if (injected_fault() == 3) {
+        *n_bad = -1;
+        return fail(GBSP_ERR_INVALID_CSR, "validate: injected failure (GBSP_FAULT=validate)");
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     void *d = nullptr;
     if ((st = scratch_alloc(&d, sizeof(unsigned long long), s))) return st;

@@ -22,6 +22,8 @@ int ok();
 void count_launches(int n);
 // Converts a pending launch error into GBSP_ERR_CUDA (with the CUDA message).
 int check_launch(const char *what);
+// Fault selected by the GBSP_FAULT environment variable (0 none, 1 alloc, 2 launch, 3 validate).
+int injected_fault();
 // SM count of the current device (cached per device).
 int sm_count();
 // Stream-ordered scratch from a library-owned pool that keeps its memory between calls.

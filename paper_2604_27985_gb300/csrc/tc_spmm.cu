@@ -163,6 +163,7 @@ struct TcArgs {
     int M, K, N;
     int *err;       // set on a timed-out wait
     int block_box;  // 1: the tensor map is the 3-D atom view (one copy per block); 0: 2-D
+    int withhold;   // testing the timeout path: window 0 never loads this chunk (-1: off)
 };
 
 template <int NT>
@@ -221,6 +222,7 @@ __global__ void __launch_bounds__(128) tc_window_kernel(const __grid_constant__ 
                 break;
             }
             uint8_t *bt = smem + s * SH::STAGE;
+            if (ch == a.withhold && blockIdx.x == 0) continue;  // nothing will complete full[s]
             mbar_expect_tx(&full[s], SH::STAGE);
             bulk_load(bt + SH::BT, a.atiles + (size_t)(b0 / kBlkPerCh + ch) * kATile, kATile, &full[s]);
 #pragma unroll 1
@@ -454,6 +456,7 @@ struct gbsp_plan {
     int32_t *res_rowptr, *res_colidx;
     uint16_t *res_vals;
     int *err;
+    int withhold;  // see gbsp_plan_test_withhold
     gbsp_opts residual_opts;
 };
 
@@ -545,6 +548,7 @@ GBSP_EXPORT int gbsp_plan_create(const gbsp_csr *A, int32_t threshold, const gbs
     p->nnz = A->nnz;
     p->threshold = threshold;
     p->residual_opts = residual_opts ? *residual_opts : gbsp_opts{};
+    p->withhold = -1;
     int st = GBSP_OK;
     int32_t *slot = nullptr, *win_nb = nullptr, *padded = nullptr, *has = nullptr, *win_off = nullptr,
             *tc_index = nullptr, *res_len = nullptr;
@@ -675,7 +679,7 @@ GBSP_EXPORT int gbsp_plan_execute(const gbsp_plan *p, const gbsp_dense *B, gbsp_
             return fail(GBSP_ERR_CUDA, "plan execute: tensor map encoding failed");
     }
     TcArgs args{p->tc_row0, p->tc_blk, p->blk_col, p->atiles, static_cast<float *>(C->data), C->ld, (int)p->M,
-                (int)p->K, (int)N, p->err, block_box};
+                (int)p->K, (int)N, p->err, block_box, p->withhold};
     switch (nt) {
         case 1: st = launch_tc<1>(map, args, p->nwin_tc, s); break;
         case 2: st = launch_tc<2>(map, args, p->nwin_tc, s); break;
@@ -702,7 +706,17 @@ GBSP_EXPORT int gbsp_plan_check(const gbsp_plan *p, void *stream) {
     if (cudaMemcpyAsync(&h, p->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return check_launch("plan check");
-    if (h) return fail(GBSP_ERR_TIMEOUT, "a tensor-core window gave up waiting (code %d)", h);
+    if (h) {
+        cudaMemsetAsync(p->err, 0, sizeof(int), s);  // report each timeout once
+        cudaStreamSynchronize(s);
+        return fail(GBSP_ERR_TIMEOUT, "a tensor-core window gave up waiting (code %d)", h);
+    }
+    return ok();
+}
+
+GBSP_EXPORT int gbsp_plan_test_withhold(gbsp_plan *p, int32_t chunk) {
+    if (!p) return fail(GBSP_ERR_INVALID_ARG, "plan test: null plan");
+    p->withhold = chunk;
     return ok();
 }
 

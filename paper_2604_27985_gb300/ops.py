@@ -181,6 +181,10 @@ class TcPlan:
     def check(self, stream=None) -> None:
         check(lib.gbsp_plan_check(self._h, _stream(stream)))
 
+    def test_withhold(self, chunk: int) -> None:
+        """Make the first dense window's wait for `chunk` run out (timeout-path testing)."""
+        check(lib.gbsp_plan_test_withhold(self._h, int(chunk)))
+
     def close(self) -> None:
         if getattr(self, "_h", None):
             lib.gbsp_plan_destroy(self._h)

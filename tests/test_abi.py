@@ -90,3 +90,30 @@ def test_argument_errors_return_without_launching(gb):
     assert lib.gbsp_quantize_bf16(None, None, -1, None) == -1
     assert lib.gbsp_quantize_e4m3_rows(None, None, 2, 4, 2, None, None, None) == -1
     assert lib.gbsp_get_last_error() == -1
+
+
+def _run_with_fault(fault, code):
+    import subprocess
+    import sys
+
+    env = dict(os.environ, GBSP_FAULT=fault)
+    r = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    return r.stdout.strip()
+
+
+def test_injected_faults_surface_as_status_codes(gb):
+    """GBSP_FAULT makes the library take its error paths before touching a GPU."""
+    code = (
+        "import ctypes\n"
+        "from paper_2604_27985_gb300 import _lib\n"
+        "lib = _lib.lib; P = ctypes.byref\n"
+        "A = _lib.Csr(4, 5, 3, 16, 16, 16, None, _lib.F32)\n"
+        "B = _lib.Dense(16, 5, 8, 8, None, _lib.F32); C = _lib.Dense(16, 4, 8, 8, None, _lib.F32)\n"
+        "X = _lib.Dense(16, 4, 8, 8, None, _lib.F32); Y = _lib.Dense(16, 5, 8, 8, None, _lib.F32)\n"
+        "bad = ctypes.c_int64(0)\n"
+        "print(lib.spmm_csr_ex(P(A), P(B), P(C), None, None), lib.sddmm_csr_ex(P(A), P(X), P(Y), 16, None, None),\n"
+        "      lib.gbsp_csr_validate(P(A), None, P(bad)), bad.value)\n")
+    assert _run_with_fault("launch", code).split()[:2] == ["-5", "-5"]
+    assert _run_with_fault("alloc", code).split()[2] == "-6"
+    assert _run_with_fault("validate", code).split()[2:] == ["-2", "-1"]

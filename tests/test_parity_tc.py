@@ -128,3 +128,26 @@ def test_tc_full_size_clustered_sampled_rows(gb):
     assert_within(C[rows], ref, sc, TOL32, "tc full size dequantised")
     ref0, sc0 = oracle.spmm(rp, ci, v, B)
     assert_within(C[rows], ref0, sc0, TOL_BF16, "tc full size vs fp32")
+
+
+def test_tc_bounded_wait_reports_timeout(gb):
+    """A stage that never arrives makes the window's MMA warp give up after about a second:
+    the kernel returns, gbsp_plan_check reports GBSP_ERR_TIMEOUT, and the next execution on
+    the same context is exact again."""
+    import time
+
+    A = gen.csr_clustered(512, 512, 0.9, seed=420)
+    vals = gen.vals_int(A.nnz, 421)
+    B = gen.dense_int(A.K, 128, 422)
+    plan = plan_of(gb, A, vals)
+    plan.test_withhold(0)
+    t0 = time.time()
+    plan.execute(bf16(B))
+    with pytest.raises(gb.GbspError, match="TIMEOUT"):
+        plan.check()
+    assert time.time() - t0 < 30
+    plan.test_withhold(-1)
+    C = plan.execute(bf16(B)).cpu().numpy()
+    plan.check()
+    want, _ = oracle.spmm(A.rowptr, A.colidx, vals, B)
+    assert np.array_equal(C.astype(np.float64), want)
