@@ -105,7 +105,8 @@ __device__ __forceinline__ float ld_stream(const float *p) { return __ldcs(p); }
 __device__ __forceinline__ uint16_t ld_stream(const uint16_t *p) { return __ldcs(reinterpret_cast<const unsigned short *>(p)); }
 __device__ __forceinline__ uint8_t ld_stream(const uint8_t *p) { return __ldcs(reinterpret_cast<const unsigned char *>(p)); }
 
-// Gathered dense rows: read-only path, 16 bytes per lane.
+// Gathered dense rows: read-only path, 16 bytes per lane.  (Skipping L1 allocation for
+// them measured 1-9% slower on the 65,536^2 and 16,384^2 workloads, so they stay cached.)
 __device__ __forceinline__ uint4 ld_gather16(const void *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
 
 // Merge-path coordinate of diagonal d over the two lists "row ends" (rowptr[1..M]) and
