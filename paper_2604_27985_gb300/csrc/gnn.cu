@@ -41,17 +41,62 @@ struct GnnArgs {
     unsigned *ticket;
 };
 
+// One group step: U edges per lane group (entries q + u * G + sub of the current chunk):
+// gather H_j, dot with H_i across the group (xor butterfly), E_ij = s_ij * dot (stored by
+// the group's first lane), then E_ij * H_j into the accumulator.
+template <int LPN, int VPL, int U>
+__device__ __forceinline__ void gnn_step(const uint4 *Hv, int64_t ldv, const bool (&colok)[VPL], int c, float s,
+                                         int q, int cnt, int sub, int sl, const float (&x)[VPL][8],
+                                         float (&acc)[VPL][8], float *E, int64_t base) {
+    constexpr int G = 32 / LPN;
+    uint4 raw[U][VPL];
+    float sj[U];
+    bool ok[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int idx = q + u * G + sub;
+        const int cj = __shfl_sync(FULL, c, idx & 31);
+        sj[u] = __shfl_sync(FULL, s, idx & 31);
+        ok[u] = idx < cnt;
+        const uint4 *rp = Hv + (int64_t)cj * ldv;
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) raw[u][v] = (ok[u] && colok[v]) ? __ldg(rp + v * LPN) : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        float f[VPL][8];
+        float dot = 0.f;
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+            BF16::unpack(raw[u][v], f[v]);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) dot = fmaf(x[v][t], f[v][t], dot);
+        }
+#pragma unroll
+        for (int off = LPN / 2; off >= 1; off >>= 1) dot += __shfl_xor_sync(FULL, dot, off);
+        const float e = sj[u] * dot;
+        if (sl == 0 && ok[u]) E[base + q + u * G + sub] = e;
+#pragma unroll
+        for (int v = 0; v < VPL; ++v)
+#pragma unroll
+            for (int t = 0; t < 8; ++t) acc[v][t] = fmaf(e, f[v][t], acc[v][t]);
+    }
+}
+
 // The rows [r0, r1) (at most 63) of one graph, one after another, with LPN lanes per edge
-// and one 16-byte BF16 vector (8 features) per lane.  The tile's row pointers sit in two
-// registers per lane; the next row's first 32 column indices and values and its H row are
-// loaded while the current row computes, so a row starts with its data in registers.
-template <int LPN, int U>
+// and VPL 16-byte BF16 vectors (8 features each) per lane.  The tile's row pointers sit in
+// two registers per lane; the next row's first 32 column indices and values and its H row
+// are loaded while the current row computes.  Full steps take U edges per group; the rest
+// of a chunk goes one edge per group, so a row with a single edge costs one step.
+template <int LPN, int VPL, int U>
 __device__ __forceinline__ void gnn_tile(const GraphDesc &g, int r0, int r1, int lane) {
     constexpr int G = 32 / LPN;
     constexpr int STEP = G * U;
     static_assert(STEP <= 32 && 32 % STEP == 0, "whole steps per chunk");
     const int sl = lane % LPN, sub = lane / LPN;
-    const bool colok = sl * 8 < g.N;
+    bool colok[VPL];
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) colok[v] = (v * LPN + sl) * 8 < g.N;
     const uint4 *Hv = reinterpret_cast<const uint4 *>(g.H) + sl;
     const int64_t ldv = g.ldh / 8;
     const int nrows = r1 - r0;
@@ -68,26 +113,35 @@ __device__ __forceinline__ void gnn_tile(const GraphDesc &g, int r0, int r1, int
         c = ld_stream(g.colidx + p0 + lane);
         s = ld_stream(g.svals + p0 + lane);
     }
-    uint4 xraw = colok ? __ldg(Hv + (int64_t)r0 * ldv) : make_uint4(0, 0, 0, 0);
+    uint4 xraw[VPL];
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) xraw[v] = colok[v] ? __ldg(Hv + (int64_t)r0 * ldv + v * LPN) : make_uint4(0, 0, 0, 0);
     for (int k = 0; k < nrows; ++k) {
         const int row = r0 + k;
         // next row, loaded now
         int64_t q1 = p1;
         int cn = 0;
         float sn = 0.f;
-        uint4 xn = make_uint4(0, 0, 0, 0);
+        uint4 xn[VPL];
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) xn[v] = make_uint4(0, 0, 0, 0);
         if (k + 1 < nrows) {
             q1 = start(k + 2);
             if (p1 + lane < q1) {
                 cn = ld_stream(g.colidx + p1 + lane);
                 sn = ld_stream(g.svals + p1 + lane);
             }
-            if (colok) xn = __ldg(Hv + (int64_t)(row + 1) * ldv);
-        }
-        float x[8], acc[8];
-        BF16::unpack(xraw, x);
 #pragma unroll
-        for (int t = 0; t < 8; ++t) acc[t] = 0.f;
+            for (int v = 0; v < VPL; ++v)
+                if (colok[v]) xn[v] = __ldg(Hv + (int64_t)(row + 1) * ldv + v * LPN);
+        }
+        float x[VPL][8], acc[VPL][8];
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+            BF16::unpack(xraw[v], x[v]);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) acc[v][t] = 0.f;
+        }
         for (int64_t base = p0; base < p1; base += 32) {
             if (base > p0) {  // rows longer than 32 edges load their later chunks here
                 c = 0;
@@ -98,57 +152,42 @@ __device__ __forceinline__ void gnn_tile(const GraphDesc &g, int r0, int r1, int
                 }
             }
             const int cnt = (int)min((int64_t)32, p1 - base);
+            int q = 0;
 #pragma unroll 1
-            for (int q = 0; q < cnt; q += STEP) {
-                uint4 raw[U];
-                float sj[U];
-                bool ok[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int idx = q + u * G + sub;
-                    const int cj = __shfl_sync(FULL, c, idx);
-                    sj[u] = __shfl_sync(FULL, s, idx);
-                    ok[u] = idx < cnt;
-                    raw[u] = (ok[u] && colok) ? __ldg(Hv + (int64_t)cj * ldv) : make_uint4(0, 0, 0, 0);
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    float f[8];
-                    BF16::unpack(raw[u], f);
-                    float dot = 0.f;
-#pragma unroll
-                    for (int t = 0; t < 8; ++t) dot = fmaf(x[t], f[t], dot);
-#pragma unroll
-                    for (int off = LPN / 2; off >= 1; off >>= 1) dot += __shfl_xor_sync(FULL, dot, off);
-                    const float e = sj[u] * dot;
-                    if (sl == 0 && ok[u]) g.E[base + q + u * G + sub] = e;
-#pragma unroll
-                    for (int t = 0; t < 8; ++t) acc[t] = fmaf(e, f[t], acc[t]);
-                }
-            }
+            for (; q + STEP <= cnt; q += STEP)
+                gnn_step<LPN, VPL, U>(Hv, ldv, colok, c, s, q, cnt, sub, sl, x, acc, g.E, base);
+#pragma unroll 1
+            for (; q < cnt; q += G) gnn_step<LPN, VPL, 1>(Hv, ldv, colok, c, s, q, cnt, sub, sl, x, acc, g.E, base);
         }
 #pragma unroll
         for (int off = LPN; off < 32; off <<= 1)
 #pragma unroll
-            for (int t = 0; t < 8; ++t) acc[t] += __shfl_xor_sync(FULL, acc[t], off);
-        if (lane < LPN && colok) {
-            uint32_t w[4];
+            for (int v = 0; v < VPL; ++v)
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                __nv_bfloat162 h = __floats2bfloat162_rn(acc[2 * t], acc[2 * t + 1]);
-                w[t] = *reinterpret_cast<uint32_t *>(&h);
+                for (int t = 0; t < 8; ++t) acc[v][t] += __shfl_xor_sync(FULL, acc[v][t], off);
+        if (lane < LPN) {
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) {
+                if (!colok[v]) continue;
+                uint32_t w[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    __nv_bfloat162 h = __floats2bfloat162_rn(acc[v][2 * t], acc[v][2 * t + 1]);
+                    w[t] = *reinterpret_cast<uint32_t *>(&h);
+                }
+                reinterpret_cast<uint4 *>(g.O + (int64_t)row * g.ldo)[v * LPN + sl] = make_uint4(w[0], w[1], w[2], w[3]);
             }
-            reinterpret_cast<uint4 *>(g.O + (int64_t)row * g.ldo)[sl] = make_uint4(w[0], w[1], w[2], w[3]);
         }
         p0 = p1;
         p1 = q1;
         c = cn;
         s = sn;
-        xraw = xn;
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) xraw[v] = xn[v];
     }
 }
 
-__global__ void __launch_bounds__(256) gnn_kernel(const GnnArgs a) {
+__global__ void __launch_bounds__(256, 3) gnn_kernel(const GnnArgs a) {
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned t = 0;
@@ -158,11 +197,11 @@ __global__ void __launch_bounds__(256) gnn_kernel(const GnnArgs a) {
         const Tile tile = a.tiles[t];
         const GraphDesc g = a.graphs[tile.graph];
         if (g.N <= 64)
-            gnn_tile<8, 4>(g, tile.row0, tile.row1, lane);
+            gnn_tile<8, 1, 4>(g, tile.row0, tile.row1, lane);
         else if (g.N <= 128)
-            gnn_tile<16, 2>(g, tile.row0, tile.row1, lane);
+            gnn_tile<8, 2, 2>(g, tile.row0, tile.row1, lane);
         else
-            gnn_tile<32, 2>(g, tile.row0, tile.row1, lane);
+            gnn_tile<16, 2, 2>(g, tile.row0, tile.row1, lane);
     }
 }
 

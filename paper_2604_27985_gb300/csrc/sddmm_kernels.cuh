@@ -20,7 +20,10 @@ __device__ __forceinline__ void sddmm_chunk(const uint4 *__restrict__ Yv, int64_
                                             const bool (&colok)[VPL], const float (&x)[VPL][EL::V],
                                             float (&part)[LPN]) {
 #pragma unroll
+    for (int t = 0; t < LPN; ++t) part[t] = 0.f;
+#pragma unroll
     for (int t = 0; t < LPN; ++t) {
+        if (CHECK_NNZ && t >= cnt) break;  // no group has an entry at this step (warp-uniform)
         const int idx = g * LPN + t;
         const int cj = __shfl_sync(FULL, c, idx);
         const uint4 *rp = Yv + (int64_t)cj * ldv;

@@ -100,10 +100,15 @@ __device__ __forceinline__ void gather_range(const SpmmProblem &P, int64_t p0, i
             for (int q = 0; q < 32; q += STEP)
                 gather_step<EL, LPN, VPL, U, CHECK_COLS, false>(Bv, ldv, c, a, q, 32, sub, colok, acc);
         } else {
+            // the row's last, partial chunk: whole steps unchecked, then one nonzero per group
             const int cnt = (int)(p1 - base);
+            int q = 0;
 #pragma unroll 1
-            for (int q = 0; q < cnt; q += STEP)
-                gather_step<EL, LPN, VPL, U, CHECK_COLS, true>(Bv, ldv, c, a, q, cnt, sub, colok, acc);
+            for (; q + STEP <= cnt; q += STEP)
+                gather_step<EL, LPN, VPL, U, CHECK_COLS, false>(Bv, ldv, c, a, q, cnt, sub, colok, acc);
+#pragma unroll 1
+            for (; q < cnt; q += G)
+                gather_step<EL, LPN, VPL, 1, CHECK_COLS, true>(Bv, ldv, c, a, q, cnt, sub, colok, acc);
         }
         base = nb;
         c = c2;
