@@ -430,7 +430,7 @@ def run_precision(args):
     stream = torch.cuda.current_stream()
     peak, _ = peaks()
     forms = {}
-    for layout in ("uniform", "clustered"):
+    for layout in args.precision_layouts.split(","):
         A = (gen.csr_uniform(16384, 16384, 0.9, seed=2001) if layout == "uniform"
              else gen.csr_clustered(16384, 16384, 0.9, seed=2002))
         B, X, Y = (gen.dense_normal(16384, 256, 2003 + k) for k in range(3))
@@ -466,12 +466,13 @@ def run_precision(args):
         plan.check()
         plan.close()
     best = max((k for k in forms if "/" in k and not k.endswith("tc_plan")), key=lambda k: forms[k]["step_gflops"])
-    base = forms["clustered/fp32"]["spmm_ms"] + forms["clustered/fp32"]["sddmm_ms"]
+    last = args.precision_layouts.split(",")[-1]
+    base = forms[f"{last}/fp32"]["spmm_ms"] + forms[f"{last}/fp32"]["sddmm_ms"]
     _line("SpMM & SDDMM GFLOP/s (2*nnz*N each), precision forms vs plain FP32", forms[best]["step_gflops"],
           "GFLOP/s", forms[best]["spmm_ms"] + forms[best]["sddmm_ms"], args, best.split("/")[1],
           {"workload": "CSR 16384x16384 at 90% (uniform seed 2001, clustered 16x8 blocks at 40% fill seed 2002), "
                        "SpMM N=256 + SDDMM Kd=256", "best_form": best,
-           "fp32_clustered_step_ms": round(base, 4)}, forms=forms)
+           f"fp32_{last}_step_ms": round(base, 4)}, forms=forms)
 
 
 def run_gnn(args):
@@ -482,7 +483,7 @@ def run_gnn(args):
     import paper_2604_27985_gb300 as gb
 
     dev = torch.device("cuda")
-    graphs = gen.gnn_batch(G=512, seed=3000)
+    graphs = gen.gnn_batch(G=512, seed=3000)[:args.gnn_graphs]
     devs, flop, gbytes = [], 0.0, 0.0
     for k, (A, N) in enumerate(graphs):
         H = torch.from_numpy(gen.dense_normal(A.M, N, 3000 * 1000 + k)).to(torch.bfloat16).to(dev)
@@ -499,8 +500,9 @@ def run_gnn(args):
     peak, _ = peaks()
     info = plan.info()
     _line("batched SDDMM->SpMM GFLOP/s (4*nnz*N over the batch)", flop / ms / 1e6, "GFLOP/s", ms, args, "bf16",
-          {"workload": "512 graphs, nodes log-uniform [1000, 50000], power-law degree (mean 16, max 2048), "
-                       "row-normalised values, BF16 features N in {64,128,256}, seed 3000", **info},
+          {"workload": f"{len(graphs)} of the 512 graphs (nodes log-uniform [1000, 50000], power-law degree "
+                       "(mean 16, max 2048), row-normalised values, BF16 features N in {64,128,256}, seed 3000)",
+           **info},
           roofline={"bound": "hbm", "kernel": "gnn_kernel, gather model", "achieved": round(gbytes / ms * 1e3, 1),
                     "peak": peak, "unit": "GB/s", "frac": round(gbytes / ms * 1e3 / peak, 4),
                     "algorithmic_bytes_per_launch": int(gbytes * 1e9)},
@@ -644,6 +646,8 @@ def main():
     ap.add_argument("--no-tuned", action="store_true")
     ap.add_argument("--e2e-chunks", type=int, default=16)
     ap.add_argument("--workload", default="csr65536", choices=["csr65536", "precision", "gnn", "selector"])
+    ap.add_argument("--precision-layouts", default="uniform,clustered")
+    ap.add_argument("--gnn-graphs", type=int, default=512)
     ap.add_argument("--selector-train", type=int, default=2000)
     ap.add_argument("--selector-test", type=int, default=200)
     ap.add_argument("--selector-steps", type=int, default=6000)
