@@ -186,6 +186,29 @@ int gbsp_plan_check(const gbsp_plan *plan, void *stream);
 int gbsp_plan_test_withhold(gbsp_plan *plan, int32_t chunk);
 void gbsp_plan_destroy(gbsp_plan *plan);
 
+/* ---- grouped SpMM / SDDMM over many problems (one persistent launch in a CUDA graph) ------- */
+
+/* G independent problems (arrays of G host-side descriptors, device data) of uneven size in
+ * one launch: SpMM C_g = A_g B_g (Eq. 1) with A_g and B_g both FP32 or both BF16 and C_g FP32,
+ * widths and leading dimensions multiples of 16 bytes, rows 16-byte aligned; or SDDMM
+ * out_g = S_g o (X_g Y_g^T) (Eq. 2) with FP32 S_g values, X_g, Y_g both FP32 or both BF16,
+ * Kd <= 256 (FP32) / 512 (BF16), out[g] device float[nnz_g].  All problems of a batch share
+ * the dense dtype.  The plan reads each rowptr to the host (synchronises the stream), builds
+ * tiles of consecutive rows with about 512 entries, and records a ticket reset plus one
+ * persistent launch into a CUDA graph that gbsp_batch_plan_execute replays (asynchronous);
+ * the plan keeps the caller's pointers.  spmm_csr_batched / sddmm_csr_batched are the
+ * one-shot forms (create, execute, synchronise, destroy). */
+typedef struct gbsp_batch_plan gbsp_batch_plan;
+int gbsp_batch_plan_create_spmm(int G, const gbsp_csr *A, const gbsp_dense *B, gbsp_dense *C, void *stream,
+                                gbsp_batch_plan **out);
+int gbsp_batch_plan_create_sddmm(int G, const gbsp_csr *S, const gbsp_dense *X, const gbsp_dense *Y,
+                                 float *const *out, void *stream, gbsp_batch_plan **plan);
+int gbsp_batch_plan_execute(const gbsp_batch_plan *plan, void *stream);
+void gbsp_batch_plan_destroy(gbsp_batch_plan *plan);
+int spmm_csr_batched(int G, const gbsp_csr *A, const gbsp_dense *B, gbsp_dense *C, void *stream);
+int sddmm_csr_batched(int G, const gbsp_csr *S, const gbsp_dense *X, const gbsp_dense *Y, float *const *out,
+                      void *stream);
+
 /* ---- batched graph chain (one persistent launch in a CUDA graph) ---------------------------- */
 
 /* For each graph g of a batch of G (arrays of G host-side descriptors, device data):

@@ -6,6 +6,9 @@ the library is not built: there is no CPU fallback.
 """
 from ._lib import GbspError, LIB_PATH  # noqa: F401
 from .ops import (  # noqa: F401
+    BatchPlan,
+    sddmm_csr_batched,
+    spmm_csr_batched,
     N_PARAMS,
     N_VARIANTS,
     autotune,

@@ -84,6 +84,14 @@ def _load() -> ctypes.CDLL:
                           ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int32), P],
         "gbsp_spmm_sddmm_host": [P, P, P, P, P, I64, P, P, P, I64, I64, I64, I64, ctypes.c_int32, ctypes.c_int32,
                                  P],
+        "gbsp_batch_plan_create_spmm": [I, ctypes.POINTER(Csr), ctypes.POINTER(Dense), ctypes.POINTER(Dense), P,
+                                        ctypes.POINTER(P)],
+        "gbsp_batch_plan_create_sddmm": [I, ctypes.POINTER(Csr), ctypes.POINTER(Dense), ctypes.POINTER(Dense),
+                                         ctypes.POINTER(P), P, ctypes.POINTER(P)],
+        "gbsp_batch_plan_execute": [P, P],
+        "spmm_csr_batched": [I, ctypes.POINTER(Csr), ctypes.POINTER(Dense), ctypes.POINTER(Dense), P],
+        "sddmm_csr_batched": [I, ctypes.POINTER(Csr), ctypes.POINTER(Dense), ctypes.POINTER(Dense),
+                              ctypes.POINTER(P), P],
         "gbsp_get_last_error": [],
         "gbsp_device_sm_count": [],
     }
@@ -91,6 +99,8 @@ def _load() -> ctypes.CDLL:
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = I
+    lib.gbsp_batch_plan_destroy.argtypes = [P]
+    lib.gbsp_batch_plan_destroy.restype = None
     lib.gbsp_gnn_plan_destroy.argtypes = [P]
     lib.gbsp_gnn_plan_destroy.restype = None
     lib.gbsp_plan_destroy.argtypes = [P]

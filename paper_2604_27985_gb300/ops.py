@@ -325,3 +325,62 @@ def spmm_sddmm_host(rowptr, colidx, vals, B=None, C=None, X=None, Y=None, out=No
     Kd = X.shape[1] if X is not None else 0
     check(lib.gbsp_spmm_sddmm_host(_hptr(rowptr), _hptr(colidx), _hptr(vals), _hptr(B), _hptr(C), N, _hptr(X),
                                    _hptr(Y), _hptr(out), Kd, M, K, nnz, int(chunks), int(slots), _stream(stream)))
+
+
+def _batch_arrays(problems, sddmm: bool):
+    G = len(problems)
+    A = (Csr * max(G, 1))()
+    D1 = (Dense * max(G, 1))()
+    D2 = (Dense * max(G, 1))()
+    outs = (ctypes.c_void_p * max(G, 1))()
+    for g, pr in enumerate(problems):
+        if sddmm:
+            rp, ci, sv, X, Y, out = pr
+            A[g] = _csr(rp, ci, sv, Y.shape[0])
+            D1[g], D2[g] = _dense(X), _dense(Y)
+            outs[g] = _ptr(out)
+        else:
+            rp, ci, v, B, C = pr
+            A[g] = _csr(rp, ci, v, B.shape[0])
+            D1[g], D2[g] = _dense(B), _dense(C)
+    return G, A, D1, D2, outs
+
+
+class BatchPlan:
+    """Grouped SpMM (problems: (rowptr, colidx, vals, B, C)) or SDDMM (problems:
+    (rowptr, colidx, svals, X, Y, out)) over many problems in one persistent launch replayed
+    from a CUDA graph."""
+
+    def __init__(self, problems, sddmm=False, stream=None):
+        self._keep = problems
+        G, A, D1, D2, outs = _batch_arrays(problems, sddmm)
+        h = ctypes.c_void_p()
+        if sddmm:
+            check(lib.gbsp_batch_plan_create_sddmm(G, A, D1, D2, outs, _stream(stream), ctypes.byref(h)))
+        else:
+            check(lib.gbsp_batch_plan_create_spmm(G, A, D1, D2, _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    def execute(self, stream=None) -> None:
+        check(lib.gbsp_batch_plan_execute(self._h, _stream(stream)))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib.gbsp_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spmm_csr_batched(problems, stream=None) -> None:
+    G, A, B, C, _ = _batch_arrays(problems, False)
+    check(lib.spmm_csr_batched(G, A, B, C, _stream(stream)))
+
+
+def sddmm_csr_batched(problems, stream=None) -> None:
+    G, S, X, Y, outs = _batch_arrays(problems, True)
+    check(lib.sddmm_csr_batched(G, S, X, Y, outs, _stream(stream)))
