@@ -231,6 +231,14 @@ def write_traffic(report, spmm_re, sddmm_re):
     print(json.dumps(t))
 
 
+def _gather_ceiling(p, nnz, kernel_ms):
+    """The kernel's gathered-row bytes per second against the gather probe's on the same
+    indices and rows (the level that binds when the gathered operand sits in L2)."""
+    achieved = nnz * p["row_bytes"] / (kernel_ms / 1e3) / 1e9
+    return {"probe": "gbsp_gather_probe over the workload's colidx", "row_bytes": p["row_bytes"],
+            "probe_gbs": p["gbs"], "kernel_gbs": round(achieved, 1), "frac": round(achieved / p["gbs"], 4)}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -344,6 +352,15 @@ def run_ours(args):
                  "bf16_step_gflops": round(flops(nnz) / ((ms_bs + ms_bd) / 1e3) / 1e9, 1),
                  "note": "BF16 operands, FP32 accumulation; parity in tests/test_parity_lowp.py"}
 
+    # the ceiling of the gather pattern itself (outside the timed region): the workload's
+    # column indices over B's and Y's rows, same lane layout, no arithmetic
+    sink = torch.empty(8 * gb.sm_count() * 256, dtype=torch.int32, device=dev)
+    probe = {}
+    for name, table, rb in (("spmm", Bd, N_SPMM * 4), ("sddmm", Yd, KD_SDDMM * 4)):
+        ms_p = min(_event_ms(lambda: gb.gather_probe(table, ci, rb, unroll=u, sink=sink, stream=stream), 20, 3, stream)
+                   for u in (4, 8))
+        probe[name] = {"row_bytes": rb, "ms": round(ms_p, 4), "gbs": round(nnz * rb / (ms_p / 1e3) / 1e9, 1)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(A, B, X, Y, budget_s=args.cpu_seconds)
@@ -368,11 +385,13 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": "spmm (Eq. 1), gather model",
                      "achieved": round(spmm_gbs, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": round(spmm_gbs / peak, 4), "traffic": traffic_spmm,
-                     "algorithmic_bytes_per_launch": spmm_bytes, "ms_per_launch": round(spmm_ms, 4)},
+                     "algorithmic_bytes_per_launch": spmm_bytes, "ms_per_launch": round(spmm_ms, 4),
+                     "gather_ceiling": _gather_ceiling(probe["spmm"], nnz, spmm_ms)},
         "roofline_sddmm": {"bound": "hbm", "kernel": "sddmm (Eq. 2), gather model",
                            "achieved": round(sddmm_gbs, 1), "peak": peak, "unit": "GB/s",
                            "frac": round(sddmm_gbs / peak, 4), "traffic": traffic_sddmm,
-                           "algorithmic_bytes_per_launch": sddmm_bytes, "ms_per_launch": round(sddmm_ms, 4)},
+                           "algorithmic_bytes_per_launch": sddmm_bytes, "ms_per_launch": round(sddmm_ms, 4),
+                           "gather_ceiling": _gather_ceiling(probe["sddmm"], nnz, sddmm_ms)},
         "roofline_compulsory_spmm": {"bytes": comp, "achieved": round(comp / (spmm_ms / 1e3) / 1e9, 1),
                                      "frac": round(comp / (spmm_ms / 1e3) / 1e9 / peak, 4)},
         "spmm_gflops": round(2.0 * nnz * N_SPMM / (spmm_ms / 1e3) / 1e9, 1),
@@ -420,7 +439,7 @@ def _line(metric, value, unit, ms, args, dtype, config, **extra):
 
 def run_precision(args):
     """16,384^2 at 90%, N = Kd = 256: SpMM + SDDMM in FP32, BF16, E4M3 (CUDA cores) and the
-    BF16 condensed-tile tensor-core plan, on the uniform and the clustered layouts."""
+    BF16 / E4M3 condensed-tile tensor-core plans, on the uniform and the clustered layouts."""
     import torch
 
     import paper_2604_27985_gb300 as gb
@@ -444,13 +463,16 @@ def run_precision(args):
         ex, ux = gb.quantize_e4m3_rows(Xd)
         ey, uy = gb.quantize_e4m3_rows(Yd)
         plan = gb.TcPlan(rp, ci, qa, A.K)
-        info = plan.info()
+        plan8 = gb.TcPlan(rp, ci, ea, A.K, row_scale=sa)
+        info, info8 = plan.info(), plan8.info()
         runs = {
             "fp32": (lambda: gb.spmm(rp, ci, v, Bd, out=C), lambda: gb.sddmm(rp, ci, v, Xd, Yd, out=out), 4, 4),
             "bf16": (lambda: gb.spmm(rp, ci, qa, qb, out=C), lambda: gb.sddmm(rp, ci, v, qx, qy, out=out), 2, 2),
             "e4m3": (lambda: gb.spmm(rp, ci, ea, eb, out=C, a_scale=sa, b_scale=sb),
                      lambda: gb.sddmm(rp, ci, v, ex, ey, out=out, x_scale=ux, y_scale=uy), 1, 1),
             "tc_bf16": (lambda: plan.execute(qb, out=C), lambda: gb.sddmm(rp, ci, v, qx, qy, out=out), 2, 2),
+            "tc_e4m3": (lambda: plan8.execute(eb, out=C, row_scale=sb),
+                        lambda: gb.sddmm(rp, ci, v, ex, ey, out=out, x_scale=ux, y_scale=uy), 1, 1),
         }
         for name, (f_spmm, f_sddmm, vb, eb_) in runs.items():
             ms_a = _event_ms(f_spmm, args.steps, args.warmup, stream)
@@ -463,9 +485,11 @@ def run_precision(args):
                 "step_gflops": round(4 * A.nnz * 256 / (ms_a + ms_b) / 1e6, 1),
                 "spmm_gather_frac": round(gbytes / (ms_a / 1e3) / peak, 3)}
         forms[f"{layout}/tc_plan"] = info
-        plan.check()
-        plan.close()
-    best = max((k for k in forms if "/" in k and not k.endswith("tc_plan")), key=lambda k: forms[k]["step_gflops"])
+        forms[f"{layout}/tc_plan_e4m3"] = info8
+        for p_ in (plan, plan8):
+            p_.check()
+            p_.close()
+    best = max((k for k in forms if "/" in k and "tc_plan" not in k), key=lambda k: forms[k]["step_gflops"])
     last = args.precision_layouts.split(",")[-1]
     base = forms[f"{last}/fp32"]["spmm_ms"] + forms[f"{last}/fp32"]["sddmm_ms"]
     _line("SpMM & SDDMM GFLOP/s (2*nnz*N each), precision forms vs plain FP32", forms[best]["step_gflops"],

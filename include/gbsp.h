@@ -156,23 +156,33 @@ int gbsp_spmm_sddmm_host(const int32_t *rowptr, const int32_t *colidx, const flo
                          float *C, int64_t N, const float *X, const float *Y, float *out, int64_t Kd, int64_t M,
                          int64_t K, int64_t nnz, int32_t chunks, int32_t slots, void *stream);
 
-/* ---- condensed-tile tensor-core plan (BF16) ----------------------------------------------- */
+/* ---- condensed-tile tensor-core plan (BF16, E4M3) ----------------------------------------- */
 
-/* A plan splits a BF16 CSR matrix A into dense 16 x 8 blocks (aligned; at least `threshold`
- * stored entries, default 16 when threshold < 1) and a residual CSR.  Executing it computes
- * C = A B (Eq. 1) as: residual SpMM through the CSR kernels (which writes C), then, for each
- * 16-row window holding dense blocks, a tcgen05 MMA of the window's condensed 16 x Kc tile
- * with the Kc gathered rows of B (BF16 operands, FP32 accumulation in tensor memory), added
- * into C.  The plan keeps its own device copy of everything it needs; A may be freed after
- * creation.  Requirements: A->dtype BF16 with strictly increasing column indices in every
- * row (GBSP_ERR_UNSUPPORTED otherwise); at execution B BF16 (K x N) and C FP32 (M x N) with
- * 64 <= N <= 512, N and B->ld multiples of 8 and B 16-byte aligned when any window is dense.
+/* A plan splits a BF16 or per-row-scaled E4M3 CSR matrix A into dense 16 x 8 blocks
+ * (aligned; at least `threshold` stored entries, default 16 when threshold < 1) and a
+ * residual CSR.  Executing it computes C = A B (Eq. 1) as: residual SpMM through the CSR
+ * kernels (which writes C), then, for each 16-row window holding dense blocks, a tcgen05 MMA
+ * of the window's condensed 16 x Kc tile with the Kc gathered rows of B (FP32 accumulation
+ * in tensor memory), added into C.  The plan keeps its own device copy of everything it
+ * needs; A (and its row scales) may be freed after creation.
+ * BF16 (kind::f16): A->dtype BF16; at execution B BF16 (K x N).
+ * E4M3 (kind::f8f6f4): A->dtype E4M3 with A->row_scale (M floats, value = s_i * q);
+ * at execution B E4M3 with B->row_scale (K floats, value = t_k * q).  A scale along the
+ * contraction cannot be applied after the MMA, so each execution first folds t into the
+ * dense-block values, a~_ik = (s_i q_ik) t_k in FP32, and requantises every window row to
+ * E4M3 with a power-of-two scale u_r (the smallest with max |a~| <= 448 u_r, at least
+ * 2^-126); the epilogue multiplies the row's MMA result by u_r.  The residual uses s and t
+ * as given.  An E4M3 plan's executions rewrite its tiles: order them on one stream.
+ * Both: strictly increasing column indices in every row (GBSP_ERR_UNSUPPORTED otherwise);
+ * C FP32 (M x N); when any window is dense, 64 <= N <= 512, N and B->ld multiples of 16
+ * bytes' worth of elements (8 BF16, 16 E4M3) and B 16-byte aligned.
  * residual_opts (may be NULL) chooses the residual kernel.  gbsp_plan_create synchronises
  * the stream; gbsp_plan_execute is asynchronous and may be repeated with new B and C.
  * Device-side waits in the tensor-core kernel give up after about a second and record it;
  * gbsp_plan_check (synchronous) returns GBSP_ERR_TIMEOUT if any did since the last check.
- * gbsp_plan_info fills info[0..4] = {dense windows, dense blocks (padded to multiples of 8
- * per window), entries inside dense blocks, residual entries, threshold}. */
+ * gbsp_plan_info fills info[0..4] = {dense windows, dense blocks (padded per window to a
+ * pipeline stage: 8 BF16 or 16 E4M3 blocks), entries inside dense blocks, residual
+ * entries, threshold}. */
 typedef struct gbsp_plan gbsp_plan;
 int gbsp_plan_create(const gbsp_csr *A, int32_t threshold, const gbsp_opts *residual_opts, void *stream,
                      gbsp_plan **out);
@@ -296,6 +306,21 @@ int gbsp_autotune(const gbsp_csr *A, const gbsp_dense *B, gbsp_dense *C, int rep
  * does not matter. */
 int spmm_csr_noalloc(const int32_t *rowptr, const int32_t *colidx, const float *vals, const float *B,
                      float *C, int64_t M, int64_t K, int64_t N, void *stream);
+
+/* ---- measurement utility (no counterpart in the paper) ------------------------------- */
+
+/* Gather-bandwidth probe: reads the rows table[idx[p]] (row_bytes = 128, 256 or 512 bytes
+ * each, consecutive rows ld_bytes apart) for p in [0, n) with the lane layout of the
+ * SpMM / SDDMM kernels (16-byte vectors, several rows in flight per lane, indices loaded
+ * coalesced and shuffled to the lane groups) and no arithmetic but an XOR per vector, so
+ * n * row_bytes / time is the ceiling of that access pattern (L2 when the table fits in it).
+ * table: device, 16-byte aligned, `rows` rows; every idx[p] must be in [0, rows) (not
+ * checked on the device).  sink: device, blocks * 256 uint32 (written, meaningless).
+ * blocks: grid size (256 threads each); unroll: 4 or 8 rows in flight per lane.
+ * Asynchronous on `stream`; GBSP_ERR_UNSUPPORTED for another row_bytes, GBSP_ERR_ALIGN for
+ * a misaligned table or ld_bytes. */
+int gbsp_gather_probe(const void *table, int64_t rows, int64_t row_bytes, int64_t ld_bytes, const int32_t *idx,
+                      int64_t n, uint32_t *sink, int32_t blocks, int32_t unroll, void *stream);
 
 /* ---- errors ------------------------------------------------------------------------ */
 

@@ -14,6 +14,7 @@ from .ops import (  # noqa: F401
     autotune,
     feature_norm,
     features,
+    gather_probe,
     mlp_predict,
     mlp_train,
     variant_options,

@@ -3,19 +3,20 @@
 //
 // Plan (once per sparsity pattern): A is cut into windows of 16 rows and each window into
 // aligned 16 x 8 blocks; a block holding at least `threshold` stored entries is dense.  A
-// window's dense blocks, in column order and padded to a multiple of 8, form a condensed
-// 16 x Kc tile of A (Kc = 8 * blocks) stored as BF16 in the shared-memory image that the
-// MMA reads (K-major, 128-byte swizzle), 16 x 64 per stage.  The remaining entries form a
-// residual CSR matrix.
+// window's dense blocks, in column order and padded to a whole pipeline stage (8 BF16 or
+// 16 E4M3 blocks), form a condensed 16 x Kc tile of A (Kc = 8 * blocks) stored in the
+// shared-memory image that the MMA reads (K-major, 128-byte swizzle, 16 rows x 128 bytes
+// per stage).  The remaining entries form a residual CSR matrix.
 //
 // Execute: the residual SpMM writes C; then one CTA per window with dense blocks computes
 //   C_w^T (N x 16) = B_g^T (N x Kc) * A_w^T (Kc x 16)
-// with tcgen05.mma kind::f16 (BF16 in, FP32 accumulate in TMEM): the feature dimension
-// is the MMA's M (128 per tile, up to 4 tiles), the 16 window rows its N, the condensed
-// columns its K.  B_g, the B rows of the dense blocks, is gathered by TMA straight into
-// the MMA's MN-major layout (8 rows x 64 features per 1 KB swizzled atom; rows past K are
-// zero-filled, which also serves the padding blocks).  The epilogue reads TMEM and adds the
-// window's 16 rows into C.
+// with tcgen05.mma (kind::f16 for BF16, kind::f8f6f4 for E4M3; FP32 accumulation in TMEM):
+// the feature dimension is the MMA's M (128 per tile, up to 4 tiles), the 16 window rows
+// its N, the condensed columns its K.  B_g, the B rows of the dense blocks, is gathered by
+// TMA (one copy per block) straight into the MMA's MN-major layout (8 rows x 128 bytes per
+// 1 KB swizzled atom; rows past K are zero-filled, which also serves the padding blocks);
+// the value tile of each stage arrives by one bulk copy.  The epilogue reads TMEM and adds
+// the window's 16 rows into C.
 #include <cuda.h>
 
 #include <mutex>
@@ -30,9 +31,10 @@ namespace tc {
 
 constexpr int kBR = 16;        // rows of a dense block (= rows of a window)
 constexpr int kBC = 8;         // columns of a dense block
-constexpr int kKCH = 64;       // condensed columns per pipeline stage
-constexpr int kBlkPerCh = kKCH / kBC;
-constexpr int kATile = kBR * kKCH * 2;  // bytes of one stage of window values
+constexpr int kATile = 2048;   // bytes of one stage of window values: 16 rows x 128 bytes
+// Dense blocks per pipeline stage: 8 for BF16 (64 condensed columns), 16 for E4M3 (128).
+template <bool FP8>
+constexpr int blocks_per_stage() { return FP8 ? 16 : 8; }
 constexpr uint64_t kWaitNs = 1000000000ull;  // a bounded wait gives up after one second
 constexpr int kStagedCols = 1024;  // block columns of a window staged in shared memory
 
@@ -83,8 +85,8 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
-// One box of a 3-D view of B: (64 features, rows, feature atoms) with the atoms outermost,
-// so one copy lands a dense block's 8 rows as NFA consecutive 1 KB MN-major atoms.
+// One box of a 3-D view of B: (128-byte feature atoms, rows, atoms) with the atoms
+// outermost, so one copy lands a dense block's 8 rows as NFA consecutive 1 KB MN-major atoms.
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
@@ -120,6 +122,16 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
         : "memory");
 }
 
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
@@ -149,9 +161,12 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
 }
 
-// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, A MN-major
-// (feature-contiguous B rows), B K-major (condensed window rows), M = 128, N = 16.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+// Instruction descriptors: FP32 accumulator, A MN-major (feature-contiguous B rows), B
+// K-major (condensed window rows), M = 128, N = 16; kind::f16 with BF16 A and B (format 1),
+// kind::f8f6f4 with E4M3 A and B (format 0).
+constexpr uint32_t kIdescBf16 =
+    (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kIdescE4m3 = (1u << 4) | (1u << 15) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
 
 struct TcArgs {
     const int32_t *win_row0;  // first row of each window that has dense blocks
@@ -164,21 +179,25 @@ struct TcArgs {
     int *err;       // set on a timed-out wait
     int block_box;  // 1: the tensor map is the 3-D atom view (one copy per block); 0: 2-D
     int withhold;   // testing the timeout path: window 0 never loads this chunk (-1: off)
+    const float *wscale;  // E4M3: scale of each window row's requantised values, else null
 };
 
-template <int NT>
+template <int NT, bool FP8>
 struct TcShape {
-    static constexpr int NFA = 2 * NT;                      // 64-feature atoms per k-row group
-    static constexpr int BT = kKCH * NT * 128 * 2;          // gathered B bytes per stage
+    static constexpr int BPS = blocks_per_stage<FP8>();     // dense blocks per stage
+    static constexpr int NFA = FP8 ? NT : 2 * NT;           // 128-byte feature atoms per 8-row group
+    static constexpr int BT = BPS * NFA * 1024;             // gathered B bytes per stage
     static constexpr int STAGE = BT + kATile;               // bytes per stage
     static constexpr int S = NT <= 2 ? 3 : 2;                  // pipeline depth (2 CTAs per SM for NT <= 2)
     static constexpr int NCOLS = NT <= 2 ? 32 : 64;         // TMEM columns (16 per feature tile)
     static constexpr int SMEM = S * STAGE + 1024 + 256;     // + alignment slack + barriers
 };
 
-template <int NT>
-__global__ void __launch_bounds__(128) tc_window_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
-    using SH = TcShape<NT>;
+constexpr int kTcThreads = 128;  // 4 warps: warp 0 lane 0 loads, warp 1 lane 0 issues MMAs, all 4 read TMEM
+
+template <int NT, bool FP8>
+__global__ void __launch_bounds__(kTcThreads) tc_window_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
+    using SH = TcShape<NT, FP8>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + SH::S * SH::STAGE);
@@ -187,16 +206,16 @@ __global__ void __launch_bounds__(128) tc_window_kernel(const __grid_constant__ 
     uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
 
     __shared__ int32_t s_cols[kStagedCols];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int w = blockIdx.x;
     const int b0 = a.win_blk[w], b1 = a.win_blk[w + 1];
-    const int nch = (b1 - b0) / kBlkPerCh;
+    const int nch = (b1 - b0) / SH::BPS;
     const int row0 = a.win_row0[w];
     // the producer reads each block's column from shared memory, not from a dependent
     // global load per TMA
-    for (int i = threadIdx.x; i < b1 - b0 && i < kStagedCols; i += blockDim.x) s_cols[i] = a.blk_col[b0 + i];
+    for (int i = tid; i < b1 - b0 && i < kStagedCols; i += blockDim.x) s_cols[i] = a.blk_col[b0 + i];
 
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         for (int s = 0; s < SH::S; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
@@ -211,8 +230,10 @@ __global__ void __launch_bounds__(128) tc_window_kernel(const __grid_constant__ 
     fence_after_sync();
     const uint32_t taddr = *tslot;
 
-    // warp 0 produces (TMA), warp 1 issues the MMAs; each runs ahead as far as the stages allow
-    if (threadIdx.x == 0) {
+    // Warp 0 produces (TMA), warp 1 issues the MMAs; each runs ahead as far as the stages
+    // allow.  (Gathering the rows with 16-byte copies from four producer warps instead
+    // measured 1.9x slower than one TMA copy per block.)
+    if (tid == 0) {
         bool ok = true;
         int issued = 0;
         for (int ch = 0; ch < nch; ++ch) {
@@ -224,10 +245,10 @@ __global__ void __launch_bounds__(128) tc_window_kernel(const __grid_constant__ 
             uint8_t *bt = smem + s * SH::STAGE;
             if (ch == a.withhold && blockIdx.x == 0) continue;  // nothing will complete full[s]
             mbar_expect_tx(&full[s], SH::STAGE);
-            bulk_load(bt + SH::BT, a.atiles + (size_t)(b0 / kBlkPerCh + ch) * kATile, kATile, &full[s]);
+            bulk_load(bt + SH::BT, a.atiles + (size_t)(b0 / SH::BPS + ch) * kATile, kATile, &full[s]);
 #pragma unroll 1
-            for (int kb = 0; kb < kBlkPerCh; ++kb) {
-                const int q = ch * kBlkPerCh + kb;
+            for (int kb = 0; kb < SH::BPS; ++kb) {
+                const int q = ch * SH::BPS + kb;
                 const int col = q < kStagedCols ? s_cols[q] : a.blk_col[b0 + q];
                 const int y = col >= 0 ? col * kBC : a.K;  // padding block: rows past K read as zeros
                 if (a.block_box) {
@@ -235,7 +256,7 @@ __global__ void __launch_bounds__(128) tc_window_kernel(const __grid_constant__ 
                 } else {
 #pragma unroll
                     for (int fa = 0; fa < SH::NFA; ++fa)
-                        tma_load_2d(bt + (kb * SH::NFA + fa) * 1024, &tmB, &full[s], 64 * fa, y);
+                        tma_load_2d(bt + (kb * SH::NFA + fa) * 1024, &tmB, &full[s], (FP8 ? 128 : 64) * fa, y);
                 }
             }
             issued = ch + 1;
@@ -244,7 +265,7 @@ __global__ void __launch_bounds__(128) tc_window_kernel(const __grid_constant__ 
         // every issued copy lands before the CTA can leave (bounded waits)
         for (int ch = issued - SH::S > 0 ? issued - SH::S : 0; ch < issued; ++ch)
             mbar_wait(&full[ch % SH::S], (ch / SH::S) & 1);
-    } else if (threadIdx.x == 32) {
+    } else if (tid == 32) {
         bool ok = true;
         for (int i = 0; i < nch; ++i) {
             const int s = i % SH::S;
@@ -255,13 +276,19 @@ __global__ void __launch_bounds__(128) tc_window_kernel(const __grid_constant__ 
             fence_after_sync();
             const uint32_t bt = smem_u32(smem + s * SH::STAGE);
             const uint32_t at = bt + SH::BT;
+            // 4 K-steps per stage: 16 BF16 or 32 E4M3 condensed columns (32 bytes of the value
+            // rows, 2 or 4 eight-row atoms of the gathered B rows) each
 #pragma unroll
-            for (int j = 0; j < kKCH / 16; ++j) {
+            for (int j = 0; j < 4; ++j) {
                 const uint64_t bdesc = smem_desc(at + j * 32, 16, 1024);
 #pragma unroll
                 for (int h = 0; h < NT; ++h) {
-                    const uint64_t adesc = smem_desc(bt + ((2 * j) * SH::NFA + 2 * h) * 1024, 1024, SH::NFA * 1024);
-                    mma_bf16(taddr + h * 16, adesc, bdesc, kIdesc, (i > 0 || j > 0) ? 1u : 0u);
+                    const int atom = FP8 ? (4 * j) * SH::NFA + h : (2 * j) * SH::NFA + 2 * h;
+                    const uint64_t adesc = smem_desc(bt + atom * 1024, 1024, SH::NFA * 1024);
+                    if constexpr (FP8)
+                        mma_e4m3(taddr + h * 16, adesc, bdesc, kIdescE4m3, (i > 0 || j > 0) ? 1u : 0u);
+                    else
+                        mma_bf16(taddr + h * 16, adesc, bdesc, kIdescBf16, (i > 0 || j > 0) ? 1u : 0u);
                 }
             }
             mma_commit(&empty[s]);
@@ -270,6 +297,7 @@ __global__ void __launch_bounds__(128) tc_window_kernel(const __grid_constant__ 
         if (!ok) atomicExch(a.err, 1);
     }
     __syncwarp();
+    // epilogue: warp w reads TMEM lanes 32w..32w+31 (features), 16 columns per tile
     const bool have = mbar_wait(done, 0);
     fence_after_sync();
     if (!have) {
@@ -284,7 +312,8 @@ __global__ void __launch_bounds__(128) tc_window_kernel(const __grid_constant__ 
 #pragma unroll
                 for (int r = 0; r < kBR; ++r) {
                     const int row = row0 + r;
-                    if (row < a.M) a.C[(int64_t)row * a.ldc + f] += v[r];
+                    const float sc = FP8 ? __ldg(a.wscale + (int64_t)w * kBR + r) : 1.0f;
+                    if (row < a.M) a.C[(int64_t)row * a.ldc + f] += v[r] * sc;
                 }
             }
         }
@@ -343,11 +372,11 @@ __global__ void __launch_bounds__(256) mark_dense_kernel(int32_t *cnt, int nbc, 
     if (threadIdx.x == 0) win_nb[w] = carry;
 }
 
-__global__ void pad_counts_kernel(const int32_t *win_nb, int nwin, int32_t *padded, int32_t *has) {
+__global__ void pad_counts_kernel(const int32_t *win_nb, int nwin, int bps, int32_t *padded, int32_t *has) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= nwin) return;
     const int n = win_nb[w];
-    padded[w] = (n + kBlkPerCh - 1) / kBlkPerCh * kBlkPerCh;
+    padded[w] = (n + bps - 1) / bps * bps;
     has[w] = n > 0 ? 1 : 0;
 }
 
@@ -372,17 +401,19 @@ __global__ void __launch_bounds__(256) fill_blocks_kernel(const int32_t *slot, i
     }
 }
 
-// Byte offset of element (r, k) of a 16 x 64 BF16 tile in the K-major 128-byte-swizzled
-// image: 8-row atoms of 1 KB, 128 B per row, 16-byte chunks XOR-ed with the row in the atom.
-__device__ __forceinline__ int atile_offset(int r, int k) {
-    const int chunk = (k * 2) >> 4;
-    return (r >> 3) * 1024 + (r & 7) * 128 + ((chunk ^ (r & 7)) << 4) + ((k * 2) & 15);
+// Byte offset of byte b of row r of a 16 x 128-byte value tile in the K-major
+// 128-byte-swizzled image: 8-row atoms of 1 KB, 128 B per row, 16-byte chunks XOR-ed with
+// the row in the atom.  (BF16: b = 2k for condensed column k; E4M3: b = k.)
+__device__ __forceinline__ int atile_offset(int r, int b) {
+    return (r >> 3) * 1024 + (r & 7) * 128 + (((b >> 4) ^ (r & 7)) << 4) + (b & 15);
 }
 
-// Scatters the entries of dense blocks into the value tiles and counts the rest per row.
-__global__ void fill_values_kernel(const int32_t *rowptr, const int32_t *colidx, const uint16_t *vals, int M,
-                                   int nbc, const int32_t *slot, const int32_t *win_off, uint8_t *atiles,
-                                   int32_t *res_len) {
+// Scatters the entries of dense blocks into the swizzled value tiles (BF16 values, or the
+// E4M3 codes that each execution folds with B's row scales and requantises) and counts the
+// rest per row.
+template <bool FP8>
+__global__ void fill_values_kernel(const int32_t *rowptr, const int32_t *colidx, const void *vals, int M, int nbc,
+                                   const int32_t *slot, const int32_t *win_off, uint8_t *tiles, int32_t *res_len) {
     const int lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= M) return;
@@ -396,9 +427,14 @@ __global__ void fill_values_kernel(const int32_t *rowptr, const int32_t *colidx,
         const int sl = s[col / kBC];
         if (sl >= 0) {
             const int blk = off + sl;
-            const int k = (blk % kBlkPerCh) * kBC + col % kBC;
-            uint8_t *tile = atiles + (int64_t)(blk / kBlkPerCh) * kATile;
-            *reinterpret_cast<uint16_t *>(tile + atile_offset(r, k)) = vals[p];
+            if constexpr (FP8) {
+                const int k = (blk % 16) * kBC + col % kBC;
+                tiles[(int64_t)(blk / 16) * kATile + atile_offset(r, k)] = static_cast<const uint8_t *>(vals)[p];
+            } else {
+                const int k = (blk % 8) * kBC + col % kBC;
+                uint8_t *tile = tiles + (int64_t)(blk / 8) * kATile;
+                *reinterpret_cast<uint16_t *>(tile + atile_offset(r, 2 * k)) = static_cast<const uint16_t *>(vals)[p];
+            }
         } else {
             ++resid;
         }
@@ -408,9 +444,9 @@ __global__ void fill_values_kernel(const int32_t *rowptr, const int32_t *colidx,
 }
 
 // Copies the residual entries of each row, in order, to the residual CSR.
-__global__ void fill_residual_kernel(const int32_t *rowptr, const int32_t *colidx, const uint16_t *vals, int M,
-                                     int nbc, const int32_t *slot, const int32_t *res_ptr, int32_t *res_col,
-                                     uint16_t *res_val) {
+template <typename T>
+__global__ void fill_residual_kernel(const int32_t *rowptr, const int32_t *colidx, const T *vals, int M, int nbc,
+                                     const int32_t *slot, const int32_t *res_ptr, int32_t *res_col, T *res_val) {
     const int lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= M) return;
@@ -435,6 +471,85 @@ __global__ void fill_residual_kernel(const int32_t *rowptr, const int32_t *colid
     }
 }
 
+// E4M3 execution, before the window kernel: for each window row r, a~_k = (s_i q_ik) t_col(k)
+// in FP32 over its condensed columns (B's per-row scale folded into A, since a scale along
+// the contraction cannot be applied after the MMA); u_r = 2^e with e the smallest exponent
+// (at least -126) for which max |a~| <= 448 u_r (1 for an empty row); the E4M3 rounding
+// (nearest-even, saturating) of a~ / u_r goes into the swizzled tiles and u_r to the
+// epilogue.  A power of two makes the division exact, so a~ already on the E4M3 grid
+// (unit scales, small integers) passes through unchanged.
+//
+// One CTA per window.  Thread t owns bytes 8t..8t+7 of every 2 KB tile of the window: one
+// row r and 8 consecutive condensed columns of one block (the swizzle permutes 16-byte
+// chunks only), read from the code tiles and written to the same offsets of the output
+// tiles.  The 16 threads sharing a row reduce its maximum with shuffles; the values are
+// recomputed in the second pass rather than held.
+__device__ __forceinline__ void fold_load_t(const float *b_scale, int col, int K, bool vec_ok, float (&t)[8]) {
+    const int64_t k0 = (int64_t)col * kBC;
+    if (col >= 0 && vec_ok && k0 + 8 <= K) {
+        const float4 lo = __ldg(reinterpret_cast<const float4 *>(b_scale + k0));
+        const float4 hi = __ldg(reinterpret_cast<const float4 *>(b_scale + k0) + 1);
+        t[0] = lo.x, t[1] = lo.y, t[2] = lo.z, t[3] = lo.w, t[4] = hi.x, t[5] = hi.y, t[6] = hi.z, t[7] = hi.w;
+    } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) t[c] = (col >= 0 && k0 + c < K) ? __ldg(b_scale + k0 + c) : 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(256) fold_e4m3_kernel(const uint8_t *__restrict__ qtiles,
+                                                        const float *__restrict__ a_scale,
+                                                        const int32_t *__restrict__ tc_row0,
+                                                        const int32_t *__restrict__ tc_blk,
+                                                        const int32_t *__restrict__ blk_col,
+                                                        const float *__restrict__ b_scale, int M, int K, int vec_ok,
+                                                        uint8_t *__restrict__ atiles, float *__restrict__ wscale) {
+    const int w = blockIdx.x, t = threadIdx.x;
+    const int b0 = tc_blk[w], ntiles = (tc_blk[w + 1] - b0) / 16;
+    const int rowin = (t >> 4) & 7, r = (t >> 7) * 8 + rowin;
+    const int kb = ((((t & 15) >> 1) ^ rowin) * 16 + 8 * (t & 1)) >> 3;  // block of the tile
+    const int row = tc_row0[w] + r;
+    const float s = row < M ? __ldg(a_scale + row) : 0.f;
+    auto values = [&](int tile, float (&v)[8]) {
+        const uint2 q = __ldg(reinterpret_cast<const uint2 *>(qtiles + (int64_t)(b0 / 16 + tile) * kATile) + t);
+        float tk[8];
+        fold_load_t(b_scale, __ldg(blk_col + b0 + tile * 16 + kb), K, vec_ok != 0, tk);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const uint8_t code = (uint8_t)(((c < 4 ? q.x : q.y) >> (8 * (c & 3))) & 0xffu);
+            v[c] = __fmul_rn(__fmul_rn(s, E4M3::value(code)), tk[c]);
+        }
+    };
+    float amax = 0.f;
+#pragma unroll 4
+    for (int tile = 0; tile < ntiles; ++tile) {
+        float v[8];
+        values(tile, v);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) amax = fmaxf(amax, fabsf(v[c]));
+    }
+    for (int off = 8; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(FULL, amax, off));
+    int e = 0;
+    if (amax > 0.f) {
+        int E;
+        const float m = frexpf(amax, &E);  // amax = m 2^E, m in [0.5, 1); 448 = 0.875 2^9
+        e = max(m <= 0.875f ? E - 9 : E - 8, -126);
+    }
+    if ((t & 15) == 0) wscale[(int64_t)w * kBR + r] = ldexpf(1.0f, e);
+    const float inv = ldexpf(1.0f, -e);
+#pragma unroll 4
+    for (int tile = 0; tile < ntiles; ++tile) {
+        float v[8];
+        values(tile, v);
+        uint32_t out[2] = {0u, 0u};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const uint32_t code = __nv_cvt_float_to_fp8(__fmul_rn(v[c], inv), __NV_SATFINITE, __NV_E4M3);
+            out[c >> 2] |= (code & 0xffu) << (8 * (c & 3));
+        }
+        reinterpret_cast<uint2 *>(atiles + (int64_t)(b0 / 16 + tile) * kATile)[t] = make_uint2(out[0], out[1]);
+    }
+}
+
 }  // namespace tc
 }  // namespace gbsp
 
@@ -445,16 +560,20 @@ using namespace gbsp::tc;
 
 struct gbsp_plan {
     int device;
+    int dtype;           // GBSP_BF16 or GBSP_E4M3
     int64_t M, K, nnz;
     int threshold;
     int nwin_tc;         // windows with dense blocks
-    int64_t nblocks;     // dense blocks, padded per window to a multiple of 8
+    int64_t nblocks;     // dense blocks, padded per window to a stage (8 BF16, 16 E4M3 blocks)
     int64_t dense_nnz;   // stored entries inside dense blocks
     int64_t res_nnz;     // residual entries
     int32_t *tc_row0, *tc_blk, *blk_col;
-    uint8_t *atiles;
+    uint8_t *atiles;     // swizzled value tiles (E4M3: rewritten by each execution)
+    uint8_t *qtiles;     // E4M3: A's codes in the same tile layout
+    float *wscale;       // E4M3: per window row scale of the requantised tiles
+    float *res_scale;    // E4M3: A's row scales (the residual's)
     int32_t *res_rowptr, *res_colidx;
-    uint16_t *res_vals;
+    void *res_vals;
     int *err;
     int withhold;  // see gbsp_plan_test_withhold
     gbsp_opts residual_opts;
@@ -479,6 +598,9 @@ void plan_free(gbsp_plan *p) {
     cudaFree(p->tc_blk);
     cudaFree(p->blk_col);
     cudaFree(p->atiles);
+    cudaFree(p->qtiles);
+    cudaFree(p->wscale);
+    cudaFree(p->res_scale);
     cudaFree(p->res_rowptr);
     cudaFree(p->res_colidx);
     cudaFree(p->res_vals);
@@ -506,19 +628,20 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-template <int NT>
+template <int NT, bool FP8>
 int launch_tc(const CUtensorMap &map, const TcArgs &args, int nwin, cudaStream_t s) {
-    using SH = TcShape<NT>;
+    using SH = TcShape<NT, FP8>;
     static bool attr_set[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return fail(GBSP_ERR_UNSUPPORTED, "tc: device ordinal %d", dev);
     if (!attr_set[dev]) {
-        if (cudaFuncSetAttribute(tc_window_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM) !=
+        if (cudaFuncSetAttribute(tc_window_kernel<NT, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, SH::SMEM) !=
             cudaSuccess)
             return check_launch("tc smem attribute");
         attr_set[dev] = true;
     }
-    tc_window_kernel<NT><<<nwin, 128, SH::SMEM, s>>>(map, args);
+    tc_window_kernel<NT, FP8><<<nwin, kTcThreads, SH::SMEM, s>>>(map, args);
     count_launches(1);
     return check_launch("tc window kernel");
 }
@@ -531,7 +654,10 @@ GBSP_EXPORT int gbsp_plan_create(const gbsp_csr *A, int32_t threshold, const gbs
     *out = nullptr;
     if (!A || A->rows < 0 || A->cols < 0 || A->nnz < 0 || A->rows > 2147483647LL || A->cols > 2147483647LL)
         return fail(GBSP_ERR_INVALID_ARG, "plan: bad CSR descriptor");
-    if (A->dtype != GBSP_BF16) return fail(GBSP_ERR_UNSUPPORTED, "plan: the tensor-core path takes BF16 values");
+    if (A->dtype != GBSP_BF16 && A->dtype != GBSP_E4M3)
+        return fail(GBSP_ERR_UNSUPPORTED, "plan: the tensor-core path takes BF16 or E4M3 values");
+    if (A->dtype == GBSP_E4M3 && A->rows > 0 && !A->row_scale)
+        return fail(GBSP_ERR_INVALID_ARG, "plan: E4M3 values need row scales");
     if (A->rows > 0 && !A->rowptr) return fail(GBSP_ERR_INVALID_ARG, "plan: null rowptr");
     if (A->nnz > 0 && (!A->colidx || !A->vals)) return fail(GBSP_ERR_INVALID_ARG, "plan: null colidx / vals");
     if (threshold < 1) threshold = 16;
@@ -541,8 +667,11 @@ GBSP_EXPORT int gbsp_plan_create(const gbsp_csr *A, int32_t threshold, const gbs
         return fail(GBSP_ERR_UNSUPPORTED, "plan: %lld windows x %lld block columns exceed the block map",
                     (long long)nwin, (long long)nbc);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool fp8 = A->dtype == GBSP_E4M3;
+    const int bps = fp8 ? blocks_per_stage<true>() : blocks_per_stage<false>();
     gbsp_plan *p = new gbsp_plan();
     cudaGetDevice(&p->device);
+    p->dtype = A->dtype;
     p->M = M;
     p->K = K;
     p->nnz = A->nnz;
@@ -575,7 +704,7 @@ GBSP_EXPORT int gbsp_plan_create(const gbsp_csr *A, int32_t threshold, const gbs
     if (M > 0) {
         count_blocks_kernel<<<row_blocks, 256, 0, s>>>(A->rowptr, A->colidx, (int)M, (int)nbc, slot, flag);
         mark_dense_kernel<<<(unsigned)nwin, 256, 0, s>>>(slot, (int)nbc, threshold, win_nb);
-        pad_counts_kernel<<<(unsigned)((nwin + 255) / 256), 256, 0, s>>>(win_nb, (int)nwin, padded, has);
+        pad_counts_kernel<<<(unsigned)((nwin + 255) / 256), 256, 0, s>>>(win_nb, (int)nwin, bps, padded, has);
         count_launches(3);
         GBSP_TRY(check_launch("plan count"));
     }
@@ -589,16 +718,27 @@ GBSP_EXPORT int gbsp_plan_create(const gbsp_csr *A, int32_t threshold, const gbs
     p->nblocks = totals[0];
     p->nwin_tc = totals[1];
     GBSP_TRY(dev_alloc(&p->blk_col, (size_t)p->nblocks));
-    GBSP_TRY(dev_alloc(&p->atiles, (size_t)(p->nblocks / kBlkPerCh) * kATile));
+    GBSP_TRY(dev_alloc(&p->atiles, (size_t)(p->nblocks / bps) * kATile));
     GBSP_TRY(dev_alloc(&p->tc_row0, (size_t)p->nwin_tc));
     GBSP_TRY(dev_alloc(&p->tc_blk, (size_t)p->nwin_tc + 1));
-    cudaMemsetAsync(p->atiles, 0, (size_t)(p->nblocks / kBlkPerCh) * kATile, s);
+    cudaMemsetAsync(p->atiles, 0, (size_t)(p->nblocks / bps) * kATile, s);
     cudaMemsetAsync(p->tc_blk, 0, sizeof(int32_t), s);
+    if (fp8) {
+        GBSP_TRY(dev_alloc(&p->qtiles, (size_t)(p->nblocks / bps) * kATile));
+        GBSP_TRY(dev_alloc(&p->wscale, (size_t)p->nwin_tc * kBR));
+        GBSP_TRY(dev_alloc(&p->res_scale, (size_t)M));
+        cudaMemsetAsync(p->qtiles, 0, (size_t)(p->nblocks / bps) * kATile, s);
+        if (M > 0) cudaMemcpyAsync(p->res_scale, A->row_scale, sizeof(float) * (size_t)M, cudaMemcpyDeviceToDevice, s);
+    }
     if (M > 0) {
         fill_blocks_kernel<<<(unsigned)nwin, 256, 0, s>>>(slot, (int)nbc, win_off, win_nb, tc_index, p->blk_col,
                                                           p->tc_row0, p->tc_blk);
-        fill_values_kernel<<<row_blocks, 256, 0, s>>>(A->rowptr, A->colidx, static_cast<const uint16_t *>(A->vals),
-                                                      (int)M, (int)nbc, slot, win_off, p->atiles, res_len);
+        if (fp8)
+            fill_values_kernel<true><<<row_blocks, 256, 0, s>>>(A->rowptr, A->colidx, A->vals, (int)M, (int)nbc, slot,
+                                                                win_off, p->qtiles, res_len);
+        else
+            fill_values_kernel<false><<<row_blocks, 256, 0, s>>>(A->rowptr, A->colidx, A->vals, (int)M, (int)nbc, slot,
+                                                                 win_off, p->atiles, res_len);
         count_launches(2);
         GBSP_TRY(check_launch("plan fill"));
     }
@@ -609,11 +749,20 @@ GBSP_EXPORT int gbsp_plan_create(const gbsp_csr *A, int32_t threshold, const gbs
     p->res_nnz = totals[0];
     p->dense_nnz = p->nnz - p->res_nnz;
     GBSP_TRY(dev_alloc(&p->res_colidx, (size_t)p->res_nnz));
-    GBSP_TRY(dev_alloc(&p->res_vals, (size_t)p->res_nnz));
+    if (fp8) {
+        GBSP_TRY(dev_alloc(reinterpret_cast<uint8_t **>(&p->res_vals), (size_t)p->res_nnz));
+    } else {
+        GBSP_TRY(dev_alloc(reinterpret_cast<uint16_t **>(&p->res_vals), (size_t)p->res_nnz));
+    }
     if (M > 0) {
-        fill_residual_kernel<<<row_blocks, 256, 0, s>>>(A->rowptr, A->colidx, static_cast<const uint16_t *>(A->vals),
-                                                        (int)M, (int)nbc, slot, p->res_rowptr, p->res_colidx,
-                                                        p->res_vals);
+        if (fp8)
+            fill_residual_kernel<uint8_t><<<row_blocks, 256, 0, s>>>(
+                A->rowptr, A->colidx, static_cast<const uint8_t *>(A->vals), (int)M, (int)nbc, slot, p->res_rowptr,
+                p->res_colidx, static_cast<uint8_t *>(p->res_vals));
+        else
+            fill_residual_kernel<uint16_t><<<row_blocks, 256, 0, s>>>(
+                A->rowptr, A->colidx, static_cast<const uint16_t *>(A->vals), (int)M, (int)nbc, slot, p->res_rowptr,
+                p->res_colidx, static_cast<uint16_t *>(p->res_vals));
         count_launches(1);
         GBSP_TRY(check_launch("plan residual"));
     }
@@ -636,56 +785,90 @@ out:
     return ok();
 }
 
-GBSP_EXPORT int gbsp_plan_execute(const gbsp_plan *p, const gbsp_dense *B, gbsp_dense *C, void *stream) {
-    if (!p || !B || !C) return fail(GBSP_ERR_INVALID_ARG, "plan execute: null argument");
-    if (B->dtype != GBSP_BF16 || C->dtype != GBSP_F32)
-        return fail(GBSP_ERR_UNSUPPORTED, "plan execute: B must be BF16 and C FP32");
-    if (B->rows != p->K || C->rows != p->M || C->cols != B->cols || B->ld < B->cols || C->ld < C->cols)
-        return fail(GBSP_ERR_INVALID_ARG, "plan execute: shape mismatch");
-    const int64_t N = B->cols;
-    if (p->nwin_tc > 0 && (N % 8 || B->ld % 8 || !aligned16(B->data) || N < 64 || N > 512))
-        return fail(GBSP_ERR_UNSUPPORTED, "plan execute: tensor-core tiles need 64 <= N <= 512, N and ld multiples "
-                                          "of 8 and a 16-byte aligned B");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // residual entries (and the overwrite of C) through the CSR kernels
-    gbsp_csr R{p->M, p->K, p->res_nnz, p->res_rowptr, p->res_colidx, p->res_vals, nullptr, GBSP_BF16};
-    int st = spmm_csr_ex(&R, B, C, &p->residual_opts, stream);
-    if (st) return st;
-    if (p->nwin_tc == 0 || N == 0) return ok();
+namespace {
+
+// The tensor map of B's rows for the window kernel: the 3-D atom view (one copy per block:
+// 128-byte feature atoms of 8 rows, atoms 128 B apart, rows ld apart) when N is a multiple
+// of 128, else a 2-D map copied one 128-byte atom at a time (features past N read as zeros).
+int encode_b_map(const gbsp_dense *B, int64_t K, bool fp8, int nt, CUtensorMap *map, int *block_box) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return fail(GBSP_ERR_CUDA, "plan execute: cuTensorMapEncodeTiled is not available");
-    const int nt = (int)((N + 127) / 128);
-    CUtensorMap map;
-    int block_box = 0;
+    const int64_t N = B->cols;
+    const int es = fp8 ? 1 : 2, atom = 128 / es;  // elements per 128-byte atom
+    const CUtensorMapDataType ty = fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    *block_box = 0;
     if (N % 128 == 0) {
-        // 3-D view: (64 features, K rows, N / 64 atoms), atoms 128 B apart, rows ld apart
-        const cuuint64_t dims3[3] = {64, (cuuint64_t)p->K, (cuuint64_t)(N / 64)};
-        const cuuint64_t strides3[2] = {(cuuint64_t)B->ld * 2, 128};
-        const cuuint32_t box3[3] = {64, 8, (cuuint32_t)(2 * nt)};
+        const int natoms = (int)(N / atom);
+        const cuuint64_t dims3[3] = {(cuuint64_t)atom, (cuuint64_t)K, (cuuint64_t)natoms};
+        const cuuint64_t strides3[2] = {(cuuint64_t)B->ld * es, 128};
+        const cuuint32_t box3[3] = {(cuuint32_t)atom, 8, (cuuint32_t)natoms};
         const cuuint32_t estr3[3] = {1, 1, 1};
-        block_box = 2 * nt == (int)(N / 64) &&
-                    enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, B->data, dims3, strides3, box3, estr3,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        *block_box = natoms == (fp8 ? nt : 2 * nt) &&
+                     enc(map, ty, 3, B->data, dims3, strides3, box3, estr3, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     }
-    if (!block_box) {
-        const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)p->K};
-        const cuuint64_t strides[1] = {(cuuint64_t)B->ld * 2};
-        const cuuint32_t box[2] = {64, 8};
+    if (!*block_box) {
+        const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)K};
+        const cuuint64_t strides[1] = {(cuuint64_t)B->ld * es};
+        const cuuint32_t box[2] = {(cuuint32_t)atom, 8};
         const cuuint32_t estr[2] = {1, 1};
-        if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, B->data, dims, strides, box, estr,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+        if (enc(map, ty, 2, B->data, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return fail(GBSP_ERR_CUDA, "plan execute: tensor map encoding failed");
     }
-    TcArgs args{p->tc_row0, p->tc_blk, p->blk_col, p->atiles, static_cast<float *>(C->data), C->ld, (int)p->M,
-                (int)p->K, (int)N, p->err, block_box, p->withhold};
+    return GBSP_OK;
+}
+
+template <bool FP8>
+int launch_tc_nt(int nt, const CUtensorMap &map, const TcArgs &args, int nwin, cudaStream_t s) {
     switch (nt) {
-        case 1: st = launch_tc<1>(map, args, p->nwin_tc, s); break;
-        case 2: st = launch_tc<2>(map, args, p->nwin_tc, s); break;
-        case 3: st = launch_tc<3>(map, args, p->nwin_tc, s); break;
-        default: st = launch_tc<4>(map, args, p->nwin_tc, s); break;
+        case 1: return launch_tc<1, FP8>(map, args, nwin, s);
+        case 2: return launch_tc<2, FP8>(map, args, nwin, s);
+        case 3: return launch_tc<3, FP8>(map, args, nwin, s);
+        default: return launch_tc<4, FP8>(map, args, nwin, s);
     }
+}
+
+}  // namespace
+
+GBSP_EXPORT int gbsp_plan_execute(const gbsp_plan *p, const gbsp_dense *B, gbsp_dense *C, void *stream) {
+    if (!p || !B || !C) return fail(GBSP_ERR_INVALID_ARG, "plan execute: null argument");
+    const bool fp8 = p->dtype == GBSP_E4M3;
+    if (B->dtype != p->dtype || C->dtype != GBSP_F32)
+        return fail(GBSP_ERR_UNSUPPORTED, "plan execute: B must have the plan's dtype (%s) and C be FP32",
+                    fp8 ? "E4M3" : "BF16");
+    if (B->rows != p->K || C->rows != p->M || C->cols != B->cols || B->ld < B->cols || C->ld < C->cols)
+        return fail(GBSP_ERR_INVALID_ARG, "plan execute: shape mismatch");
+    if (fp8 && B->rows > 0 && !B->row_scale) return fail(GBSP_ERR_INVALID_ARG, "plan execute: E4M3 B needs row scales");
+    const int64_t N = B->cols;
+    const int amul = fp8 ? 16 : 8;  // elements per 16 bytes
+    if (p->nwin_tc > 0 && (N % amul || B->ld % amul || !aligned16(B->data) || N < 64 || N > 512))
+        return fail(GBSP_ERR_UNSUPPORTED, "plan execute: tensor-core tiles need 64 <= N <= 512, N and ld multiples "
+                                          "of %d and a 16-byte aligned B",
+                    amul);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // residual entries (and the overwrite of C) through the CSR kernels
+    gbsp_csr R{p->M, p->K, p->res_nnz, p->res_rowptr, p->res_colidx, p->res_vals, p->res_scale, p->dtype};
+    int st = spmm_csr_ex(&R, B, C, &p->residual_opts, stream);
+    if (st) return st;
+    if (p->nwin_tc == 0 || N == 0) return ok();
+    const int nt = (int)((N + 127) / 128);
+    CUtensorMap map;
+    int block_box = 0;
+    if ((st = encode_b_map(B, p->K, fp8, nt, &map, &block_box))) return st;
+    if (fp8) {
+        const float *t = static_cast<const float *>(B->row_scale);
+        fold_e4m3_kernel<<<(unsigned)p->nwin_tc, 256, 0, s>>>(p->qtiles, p->res_scale, p->tc_row0, p->tc_blk,
+                                                              p->blk_col, t, (int)p->M, (int)p->K, aligned16(t) ? 1 : 0,
+                                                              p->atiles, p->wscale);
+        count_launches(1);
+        if ((st = check_launch("tc fold"))) return st;
+    }
+    TcArgs args{p->tc_row0, p->tc_blk, p->blk_col, p->atiles, static_cast<float *>(C->data), C->ld, (int)p->M,
+                (int)p->K, (int)N, p->err, block_box, p->withhold, p->wscale};
+    st = fp8 ? launch_tc_nt<true>(nt, map, args, p->nwin_tc, s) : launch_tc_nt<false>(nt, map, args, p->nwin_tc, s);
     return st ? st : ok();
 }
 

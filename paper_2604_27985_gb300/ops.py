@@ -152,23 +152,24 @@ def launch_count() -> int:
 
 
 class TcPlan:
-    """Condensed-tile tensor-core plan of a BF16 CSR matrix (gbsp_plan_create): dense 16 x 8
-    blocks run on tcgen05, the rest on the CSR kernels.  ``execute(B)`` returns C = A B."""
+    """Condensed-tile tensor-core plan of a BF16 or per-row-scaled E4M3 CSR matrix
+    (gbsp_plan_create): dense 16 x 8 blocks run on tcgen05, the rest on the CSR kernels.
+    ``execute(B)`` returns C = A B (E4M3: ``execute(B, row_scale=t)``)."""
 
-    def __init__(self, rowptr, colidx, vals, ncols, threshold=0, *, residual_variant="auto", residual_vecs=0,
-                 residual_unroll=0, stream=None):
+    def __init__(self, rowptr, colidx, vals, ncols, threshold=0, *, row_scale=None, residual_variant="auto",
+                 residual_vecs=0, residual_unroll=0, stream=None):
         self.M = rowptr.numel() - 1
         self.K = int(ncols)
-        A = _csr(rowptr, colidx, vals, ncols)
+        A = _csr(rowptr, colidx, vals, ncols, row_scale)
         o = _opts(residual_variant, False, residual_unroll, 0, residual_vecs)
         h = ctypes.c_void_p()
         check(lib.gbsp_plan_create(ctypes.byref(A), int(threshold), ctypes.byref(o), _stream(stream), ctypes.byref(h)))
         self._h = h
 
-    def execute(self, B, out=None, stream=None) -> torch.Tensor:
+    def execute(self, B, out=None, row_scale=None, stream=None) -> torch.Tensor:
         if out is None:
             out = torch.empty((self.M, B.shape[1]), dtype=torch.float32, device=B.device)
-        b, c = _dense(B), _dense(out)
+        b, c = _dense(B, row_scale), _dense(out)
         check(lib.gbsp_plan_execute(self._h, ctypes.byref(b), ctypes.byref(c), _stream(stream)))
         return out
 
@@ -384,3 +385,16 @@ def spmm_csr_batched(problems, stream=None) -> None:
 def sddmm_csr_batched(problems, stream=None) -> None:
     G, S, X, Y, outs = _batch_arrays(problems, True)
     check(lib.sddmm_csr_batched(G, S, X, Y, outs, _stream(stream)))
+
+
+def gather_probe(table, idx, row_bytes, *, blocks=0, unroll=4, sink=None, stream=None) -> None:
+    """Gather-bandwidth probe (gbsp_gather_probe): reads table[idx[p]] rows of row_bytes
+    bytes with the SpMM / SDDMM lane layout and no arithmetic; time it to get the ceiling
+    of the gather pattern.  ``blocks`` defaults to 8 per SM."""
+    if blocks <= 0:
+        blocks = 8 * sm_count()
+    if sink is None or sink.numel() < blocks * 256:
+        sink = torch.empty(blocks * 256, dtype=torch.int32, device=table.device)
+    ld = table.stride(0) * table.element_size()
+    check(lib.gbsp_gather_probe(_ptr(table), table.shape[0], int(row_bytes), int(ld), _ptr(idx), idx.numel(),
+                                _ptr(sink), int(blocks), int(unroll), _stream(stream)))
