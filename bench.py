@@ -306,7 +306,7 @@ def run_ours(args):
 
     def e2e_step():
         gb.spmm_sddmm_host(h_rp, h_ci, h_v, B=h_B, C=h_C, X=h_X, Y=h_Y, out=h_out, chunks=args.e2e_chunks,
-                           slots=3, stream=stream)
+                           slots=args.e2e_slots, stream=stream)
 
     for _ in range(max(1, args.warmup)):
         e2e_step()
@@ -668,7 +668,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tuned", action="store_true")
-    ap.add_argument("--e2e-chunks", type=int, default=16)
+    ap.add_argument("--e2e-chunks", type=int, default=8)
+    ap.add_argument("--e2e-slots", type=int, default=4)
     ap.add_argument("--workload", default="csr65536", choices=["csr65536", "precision", "gnn", "selector"])
     ap.add_argument("--precision-layouts", default="uniform,clustered")
     ap.add_argument("--gnn-graphs", type=int, default=512)

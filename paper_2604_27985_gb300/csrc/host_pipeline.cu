@@ -7,7 +7,8 @@
 // rows goes through one of `slots` device buffers (row pointers, column indices, values,
 // its C rows and its SDDMM outputs); events order copy -> compute -> copy-back per chunk,
 // and a slot is refilled only after its previous chunk's results have left the device.  The
-// dense operands (B for SpMM, X and Y for SDDMM) are copied once at the start.  Column
+// gathered dense operands (B for SpMM, Y for SDDMM) are copied once at the start; the rows
+// of X travel with their chunk.  Column
 // indices and values of chunk [r0, r1) sit at device offset 0 while the kernels index
 // them with the matrix's absolute entry numbers, so the kernels get base pointers moved
 // back by rowptr[r0].
@@ -23,6 +24,56 @@ struct Slot {
     int32_t *rowptr = nullptr, *colidx = nullptr;
     float *vals = nullptr, *C = nullptr, *out = nullptr;
     cudaEvent_t copied = nullptr, computed = nullptr, drained = nullptr;
+};
+
+// The streams and events of the pipeline, created once per host thread and device and
+// reused by every call (calls from one thread are ordered through the caller's stream, so
+// they never use them concurrently).
+struct Executor {
+    int device = -1;
+    cudaStream_t in = nullptr, run = nullptr, out = nullptr;
+    cudaEvent_t ready = nullptr, dense_in = nullptr, all_out = nullptr;
+    std::vector<Slot> slots;  // events only; buffers are taken per call
+
+    int prepare(int dev, int nslots) {
+        if (device != dev) {
+            release();
+            device = dev;
+            if (cudaStreamCreateWithFlags(&in, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaStreamCreateWithFlags(&run, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaStreamCreateWithFlags(&out, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&dense_in, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&all_out, cudaEventDisableTiming) != cudaSuccess) {
+                release();
+                return check_launch("host pipeline streams");
+            }
+        }
+        while ((int)slots.size() < nslots) {
+            Slot x;
+            if (cudaEventCreateWithFlags(&x.copied, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&x.computed, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&x.drained, cudaEventDisableTiming) != cudaSuccess)
+                return check_launch("host pipeline events");
+            slots.push_back(x);
+        }
+        return GBSP_OK;
+    }
+    void release() {
+        for (auto &x : slots) {
+            if (x.copied) cudaEventDestroy(x.copied);
+            if (x.computed) cudaEventDestroy(x.computed);
+            if (x.drained) cudaEventDestroy(x.drained);
+        }
+        slots.clear();
+        for (cudaEvent_t e : {ready, dense_in, all_out})
+            if (e) cudaEventDestroy(e);
+        for (cudaStream_t t : {in, run, out})
+            if (t) cudaStreamDestroy(t);
+        in = run = out = nullptr;
+        ready = dense_in = all_out = nullptr;
+        device = -1;
+    }
 };
 
 }  // namespace
@@ -65,22 +116,19 @@ GBSP_EXPORT int gbsp_spmm_sddmm_host(const int32_t *rowptr, const int32_t *colid
         max_rows = std::max(max_rows, bounds[c + 1] - bounds[c]);
         max_nnz = std::max(max_nnz, (int64_t)(rowptr[bounds[c + 1]] - rowptr[bounds[c]]));
     }
-    cudaStream_t s_in = nullptr, s_run = nullptr, s_out = nullptr;
-    std::vector<Slot> sl(slots);
+    static thread_local Executor ex;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return check_launch("host pipeline device");
+    int st = ex.prepare(dev, slots);
+    if (st) return st;
+    cudaStream_t s_in = ex.in, s_run = ex.run, s_out = ex.out;
+    cudaEvent_t ready = ex.ready, dense_in = ex.dense_in, all_out = ex.all_out;
+    std::vector<Slot> sl(ex.slots.begin(), ex.slots.begin() + slots);
     void *dB = nullptr, *dX = nullptr, *dY = nullptr;
-    int st = GBSP_OK;
-    cudaEvent_t ready = nullptr, dense_in = nullptr, all_out = nullptr;
 #define GBSP_CU(x)                                                             \
     do {                                                                       \
         if ((x) != cudaSuccess && st == GBSP_OK) st = check_launch("host pipeline"); \
     } while (0)
-    GBSP_CU(cudaStreamCreateWithFlags(&s_in, cudaStreamNonBlocking));
-    GBSP_CU(cudaStreamCreateWithFlags(&s_run, cudaStreamNonBlocking));
-    GBSP_CU(cudaStreamCreateWithFlags(&s_out, cudaStreamNonBlocking));
-    GBSP_CU(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
-    GBSP_CU(cudaEventCreateWithFlags(&dense_in, cudaEventDisableTiming));
-    GBSP_CU(cudaEventCreateWithFlags(&all_out, cudaEventDisableTiming));
-    if (st) goto done;
     // everything starts after the work already queued on the caller's stream
     GBSP_CU(cudaEventRecord(ready, user));
     GBSP_CU(cudaStreamWaitEvent(s_in, ready, 0));
@@ -93,9 +141,6 @@ GBSP_EXPORT int gbsp_spmm_sddmm_host(const int32_t *rowptr, const int32_t *colid
             st = GBSP_ERR_OOM;
             goto done;
         }
-        GBSP_CU(cudaEventCreateWithFlags(&x.copied, cudaEventDisableTiming));
-        GBSP_CU(cudaEventCreateWithFlags(&x.computed, cudaEventDisableTiming));
-        GBSP_CU(cudaEventCreateWithFlags(&x.drained, cudaEventDisableTiming));
     }
     if (do_spmm && scratch_alloc(&dB, sizeof(float) * (size_t)(K * N), s_in)) st = GBSP_ERR_OOM;
     if (!st && do_sddmm &&
@@ -104,10 +149,7 @@ GBSP_EXPORT int gbsp_spmm_sddmm_host(const int32_t *rowptr, const int32_t *colid
         st = GBSP_ERR_OOM;
     if (st) goto done;
     if (do_spmm) GBSP_CU(cudaMemcpyAsync(dB, B, sizeof(float) * (size_t)(K * N), cudaMemcpyHostToDevice, s_in));
-    if (do_sddmm) {
-        GBSP_CU(cudaMemcpyAsync(dX, X, sizeof(float) * (size_t)(M * Kd), cudaMemcpyHostToDevice, s_in));
-        GBSP_CU(cudaMemcpyAsync(dY, Y, sizeof(float) * (size_t)(K * Kd), cudaMemcpyHostToDevice, s_in));
-    }
+    if (do_sddmm) GBSP_CU(cudaMemcpyAsync(dY, Y, sizeof(float) * (size_t)(K * Kd), cudaMemcpyHostToDevice, s_in));
     GBSP_CU(cudaEventRecord(dense_in, s_in));
     GBSP_CU(cudaStreamWaitEvent(s_run, dense_in, 0));
     for (int c = 0; c < chunks && !st; ++c) {
@@ -116,6 +158,9 @@ GBSP_EXPORT int gbsp_spmm_sddmm_host(const int32_t *rowptr, const int32_t *colid
         const int64_t p0 = rowptr[r0], p1 = rowptr[r1], ne = p1 - p0;
         if (c >= slots) GBSP_CU(cudaStreamWaitEvent(s_in, x.drained, 0));  // slot's previous results are out
         GBSP_CU(cudaMemcpyAsync(x.rowptr, rowptr + r0, sizeof(int32_t) * (size_t)(mr + 1), cudaMemcpyHostToDevice, s_in));
+        if (do_sddmm)  // X rows of the chunk, into the full-size X buffer (never reused)
+            GBSP_CU(cudaMemcpyAsync(static_cast<float *>(dX) + r0 * Kd, X + r0 * Kd, sizeof(float) * (size_t)(mr * Kd),
+                                    cudaMemcpyHostToDevice, s_in));
         if (ne > 0) {
             GBSP_CU(cudaMemcpyAsync(x.colidx, colidx + p0, sizeof(int32_t) * (size_t)ne, cudaMemcpyHostToDevice, s_in));
             GBSP_CU(cudaMemcpyAsync(x.vals, vals + p0, sizeof(float) * (size_t)ne, cudaMemcpyHostToDevice, s_in));
@@ -174,18 +219,14 @@ done:
         scratch_free(x.vals, s_out);
         scratch_free(x.C, s_out);
         scratch_free(x.out, s_out);
-        if (x.copied) cudaEventDestroy(x.copied);
-        if (x.computed) cudaEventDestroy(x.computed);
-        if (x.drained) cudaEventDestroy(x.drained);
     }
     scratch_free(dB, s_out);
     scratch_free(dX, s_out);
     scratch_free(dY, s_out);
-    if (ready) cudaEventDestroy(ready);
-    if (dense_in) cudaEventDestroy(dense_in);
-    if (all_out) cudaEventDestroy(all_out);
-    if (s_in) cudaStreamDestroy(s_in);
-    if (s_run) cudaStreamDestroy(s_run);
-    if (s_out) cudaStreamDestroy(s_out);
+    if (st) {  // leave the executor's streams idle for the next call
+        cudaStreamSynchronize(s_in);
+        cudaStreamSynchronize(s_run);
+        cudaStreamSynchronize(s_out);
+    }
     return st ? st : ok();
 }
