@@ -533,6 +533,51 @@ def run_gnn(args):
           gpu_launches_per_step=int(launches))
 
 
+def run_batched(args):
+    """Grouped SpMM and SDDMM over the 512 graphs of the batched configuration (BF16 H of
+    width 64/128/256, FP32 outputs): one persistent launch per operation from a CUDA graph
+    (gbsp_batch_plan_*) against one launch per graph through spmm_csr_ex / sddmm_csr_ex."""
+    import torch
+
+    import paper_2604_27985_gb300 as gb
+
+    dev = torch.device("cuda")
+    graphs = gen.gnn_batch(G=512, seed=3000)[:args.gnn_graphs]
+    sp, sd, flop = [], [], 0.0
+    for k, (A, N) in enumerate(graphs):
+        H = torch.from_numpy(gen.dense_normal(A.M, N, 3000 * 1000 + k)).to(torch.bfloat16).to(dev)
+        rp, ci = torch.from_numpy(A.rowptr).to(dev), torch.from_numpy(A.colidx).to(dev)
+        v = torch.from_numpy(A.vals).to(dev)
+        sp.append((rp, ci, v.to(torch.bfloat16), H, torch.empty((A.M, N), device=dev)))
+        sd.append((rp, ci, v, H, H, torch.empty(max(A.nnz, 1), device=dev)))
+        flop += 2.0 * A.nnz * N
+    stream = torch.cuda.current_stream()
+    p_sp, p_sd = gb.BatchPlan(sp), gb.BatchPlan(sd, sddmm=True)
+    ms_sp = _event_ms(p_sp.execute, args.steps, args.warmup, stream)
+    ms_sd = _event_ms(p_sd.execute, args.steps, args.warmup, stream)
+
+    def loop_spmm():
+        for rp, ci, v, H, C in sp:
+            gb.spmm(rp, ci, v, H, out=C, stream=stream)
+
+    def loop_sddmm():
+        for rp, ci, v, X, Y, out in sd:
+            gb.sddmm(rp, ci, v, X, Y, out=out, stream=stream)
+
+    steps = max(3, args.steps // 10)
+    ms_lsp = _event_ms(loop_spmm, steps, 2, stream)
+    ms_lsd = _event_ms(loop_sddmm, steps, 2, stream)
+    _line("batched SpMM + SDDMM GFLOP/s (2*nnz*N each) over many graphs", 2 * flop / (ms_sp + ms_sd) / 1e6,
+          "GFLOP/s", ms_sp + ms_sd, args, "bf16",
+          {"workload": f"{len(graphs)} of the 512 graphs (nodes log-uniform [1000, 50000], power-law degree "
+                       "(mean 16, max 2048), row-normalised values, BF16 H of width N in {64,128,256}, seed 3000); "
+                       "SpMM S H and SDDMM S o (H H^T), FP32 outputs"},
+          grouped={"spmm_ms": round(ms_sp, 4), "sddmm_ms": round(ms_sd, 4), "launches_per_op": 1},
+          per_graph_launches={"spmm_ms": round(ms_lsp, 4), "sddmm_ms": round(ms_lsd, 4),
+                              "launches_per_op": len(graphs)},
+          speedup={"spmm": round(ms_lsp / ms_sp, 3), "sddmm": round(ms_lsd / ms_sd, 3)})
+
+
 def run_selector(args):
     """Learned selector: 2,000 training and 200 held-out corpus matrices, labels from the
     exhaustive autotuner, the MLP trained by the library's kernels; regret vs exhaustive."""
@@ -611,9 +656,22 @@ def cpu_baseline(A, B, X, Y, budget_s=15.0):
         total += dt
         work += flops(nz)
         reps += 1
+    # the small configuration (1,024^2 at 90%, N = Kd = 64) on one thread, mean of 5 runs
+    a1 = gen.csr_uniform(1024, 1024, 0.9, seed=0)
+    b1, x1, y1 = (gen.dense_normal(1024, 64, 1 + k).astype(np.float64) for k in range(3))
+    t1 = []
+    for _ in range(5):
+        t0 = time.perf_counter()
+        oracle.spmm(a1.rowptr, a1.colidx, a1.vals.astype(np.float64), b1, threads=1)
+        oracle.sddmm(a1.rowptr, a1.colidx, a1.vals.astype(np.float64), x1, y1, threads=1)
+        t1.append(time.perf_counter() - t0)
     return {"value": round(work / total / 1e9, 3), "unit": "GFLOP/s", "cores": threads, "kind": "oracle",
             "sample": f"rows [0, {r}) of the workload ({nz} nonzeros), FP64 SpMM N={N_SPMM} + SDDMM "
-                      f"Kd={KD_SDDMM}, {reps} repetitions in {total:.1f} s", "seconds": round(total, 2)}
+                      f"Kd={KD_SDDMM}, {reps} repetitions in {total:.1f} s", "seconds": round(total, 2),
+            "one_thread_1024sq_90pct": {"gflops": round(4.0 * a1.nnz * 64 / np.mean(t1) / 1e9, 3),
+                                        "ms": round(1e3 * float(np.mean(t1)), 3),
+                                        "sample": "CSR 1024x1024 at 90% (seed 0), SpMM N=64 + SDDMM Kd=64, "
+                                                  "mean of 5 runs, 1 thread"}}
 
 
 def run_reference(args):
@@ -670,7 +728,7 @@ def main():
     ap.add_argument("--no-tuned", action="store_true")
     ap.add_argument("--e2e-chunks", type=int, default=8)
     ap.add_argument("--e2e-slots", type=int, default=4)
-    ap.add_argument("--workload", default="csr65536", choices=["csr65536", "precision", "gnn", "selector"])
+    ap.add_argument("--workload", default="csr65536", choices=["csr65536", "precision", "gnn", "batched", "selector"])
     ap.add_argument("--precision-layouts", default="uniform,clustered")
     ap.add_argument("--gnn-graphs", type=int, default=512)
     ap.add_argument("--selector-train", type=int, default=2000)
@@ -691,6 +749,8 @@ def main():
         run_precision(args)
     elif args.workload == "gnn":
         run_gnn(args)
+    elif args.workload == "batched":
+        run_batched(args)
     elif args.workload == "selector":
         run_selector(args)
     else:
