@@ -61,7 +61,9 @@ typedef enum {
     GBSP_VARIANT_AUTO = 0,
     GBSP_VARIANT_ROWSPLIT = 1, /* one warp per row, vectorised gathers */
     GBSP_VARIANT_MERGE = 2,    /* nnz-balanced merge-path split with a carry fix-up pass */
-    GBSP_VARIANT_SCALAR = 3    /* unvectorised, any width / alignment */
+    GBSP_VARIANT_SCALAR = 3,   /* unvectorised, any width / alignment */
+    GBSP_VARIANT_ENTRY = 4     /* SDDMM only: stored entries split evenly across warps regardless of
+                                  rows (short or skewed rows); GBSP_ERR_UNSUPPORTED for SpMM */
 } gbsp_variant;
 
 /* A sparse matrix in CSR form (all pointers device). */
@@ -196,16 +198,19 @@ int gbsp_plan_check(const gbsp_plan *plan, void *stream);
 int gbsp_plan_test_withhold(gbsp_plan *plan, int32_t chunk);
 void gbsp_plan_destroy(gbsp_plan *plan);
 
-/* ---- grouped SpMM / SDDMM over many problems (one persistent launch in a CUDA graph) ------- */
+/* ---- grouped SpMM / SDDMM over many problems (persistent launches in one CUDA graph) ------- */
 
 /* G independent problems (arrays of G host-side descriptors, device data) of uneven size in
- * one launch: SpMM C_g = A_g B_g (Eq. 1) with A_g and B_g both FP32 or both BF16 and C_g FP32,
+ * one graph: SpMM C_g = A_g B_g (Eq. 1) with A_g and B_g both FP32 or both BF16 and C_g FP32,
  * widths and leading dimensions multiples of 16 bytes, rows 16-byte aligned; or SDDMM
  * out_g = S_g o (X_g Y_g^T) (Eq. 2) with FP32 S_g values, X_g, Y_g both FP32 or both BF16,
  * Kd <= 256 (FP32) / 512 (BF16), out[g] device float[nnz_g].  All problems of a batch share
  * the dense dtype.  The plan reads each rowptr to the host (synchronises the stream), builds
- * tiles of consecutive rows with about 512 entries, and records a ticket reset plus one
- * persistent launch into a CUDA graph that gbsp_batch_plan_execute replays (asynchronous);
+ * tiles of consecutive rows with about 512 entries, groups them by the lane layout their
+ * problem's width needs, and records the ticket resets plus one persistent launch per
+ * layout in use (at most 3 for SpMM, 5 for SDDMM) into a CUDA graph that
+ * gbsp_batch_plan_execute replays (asynchronous); SDDMM tiles of short rows (under 32
+ * entries on average) run the entry split (GBSP_VARIANT_ENTRY);
  * the plan keeps the caller's pointers.  spmm_csr_batched / sddmm_csr_batched are the
  * one-shot forms (create, execute, synchronise, destroy). */
 typedef struct gbsp_batch_plan gbsp_batch_plan;

@@ -23,7 +23,7 @@ STATUS = {
     -7: "GBSP_ERR_TIMEOUT",
 }
 F32, BF16, E4M3 = 0, 1, 2
-VARIANTS = {"auto": 0, "rowsplit": 1, "merge": 2, "scalar": 3}
+VARIANTS = {"auto": 0, "rowsplit": 1, "merge": 2, "scalar": 3, "entry": 4}
 
 
 class GbspError(RuntimeError):

@@ -182,6 +182,8 @@ GBSP_EXPORT int spmm_csr_ex(const gbsp_csr *A, const gbsp_dense *B, gbsp_dense *
     if (variant != GBSP_VARIANT_SCALAR && !vec)
         return fail(GBSP_ERR_ALIGN, "spmm: vectorised variant needs 16-byte aligned B and C, and N and ld "
                                     "multiples of %d", elems_per_vec(B->dtype));
+    if (variant == GBSP_VARIANT_ENTRY)
+        return fail(GBSP_ERR_UNSUPPORTED, "spmm: the entry split is an SDDMM variant (SpMM rows need one owner)");
     if (variant < GBSP_VARIANT_ROWSPLIT || variant > GBSP_VARIANT_SCALAR)
         return fail(GBSP_ERR_INVALID_ARG, "spmm: unknown variant %d", variant);
     SpmmProblem p{};
@@ -228,11 +230,14 @@ GBSP_EXPORT int sddmm_csr_ex(const gbsp_csr *S, const gbsp_dense *X, const gbsp_
     const int V = elems_per_vec(X->dtype);
     const bool vec = vec_ok(X) && vec_ok(Y) && X->cols > 0 && X->cols <= 32 * 16;
     int variant = o.variant;
-    if (variant == GBSP_VARIANT_AUTO) variant = vec ? GBSP_VARIANT_ROWSPLIT : GBSP_VARIANT_SCALAR;
-    if ((variant == GBSP_VARIANT_ROWSPLIT || variant == GBSP_VARIANT_MERGE) && !vec)
+    // rows shorter than a 32-entry chunk on average leave lanes idle in the row split
+    if (variant == GBSP_VARIANT_AUTO)
+        variant = !vec ? GBSP_VARIANT_SCALAR
+                       : (S->nnz >= 0 && S->nnz < 32 * S->rows ? GBSP_VARIANT_ENTRY : GBSP_VARIANT_ROWSPLIT);
+    if (variant != GBSP_VARIANT_SCALAR && !vec)
         return fail(GBSP_ERR_ALIGN, "sddmm: vectorised variant needs 16-byte aligned X and Y, Kd and ld "
                                     "multiples of %d and Kd <= %d", V, 32 * 16);
-    if (variant < GBSP_VARIANT_ROWSPLIT || variant > GBSP_VARIANT_SCALAR)
+    if (variant < GBSP_VARIANT_ROWSPLIT || variant > GBSP_VARIANT_ENTRY)
         return fail(GBSP_ERR_INVALID_ARG, "sddmm: unknown variant %d", variant);
     SddmmProblem p{};
     p.M = (int32_t)S->rows;

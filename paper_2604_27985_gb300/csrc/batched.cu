@@ -1,10 +1,13 @@
 // Grouped SpMM and SDDMM over many problems of uneven size in one persistent launch.
 //
 // The work list holds tiles of consecutive rows of one problem with about 512 stored
-// entries each; warps take tiles from an atomic ticket (reset by the launch's own recorded
-// memset) and run the row-split row kernels of spmm_kernels.cuh / sddmm_kernels.cuh on them
-// with a lane layout picked per problem from its width.  The ticket reset and the launch are
-// recorded once into a CUDA graph; executing a plan replays it.
+// entries each, grouped by the lane layout their problem's width needs (one class per
+// layout).  Each class runs as one persistent launch whose warps take tiles from the class's
+// atomic ticket and run the row kernels of spmm_kernels.cuh / sddmm_kernels.cuh on them (for
+// SDDMM tiles of short rows, the entry split).  One kernel per layout keeps each launch's
+// registers to what its layout needs (a single kernel holding every layout needed 255 and
+// spilled).  The ticket resets and the launches are recorded once into a CUDA graph;
+// executing a plan replays it.
 #include <vector>
 
 #include "sddmm_kernels.cuh"
@@ -22,10 +25,20 @@ enum Kind { kSpmm = 0, kSddmm = 1 };
 struct GroupArgs {
     const SpmmProblem *spmm;
     const SddmmProblem *sddmm;
-    const Tile *tiles;
+    const Tile *tiles;  // this class's tiles
     int ntiles;
-    unsigned *ticket;
+    unsigned *ticket;   // this class's ticket
 };
+
+constexpr int kClasses = 5;
+
+// Lane-layout class of a problem from its vectors per dense row: SpMM 0: <= 8 (8 lanes x 1),
+// 1: <= 16 (8 x 2), 2: wider (16 x 2 per 32-vector column tile); SDDMM 0: <= 4 (4 x 1),
+// 1: <= 8 (8 x 1), 2: <= 16 (8 x 2), 3: <= 32 (16 x 2), 4: <= 64 (32 x 2).
+int layout_class(int kind, int nvec) {
+    if (kind == kSpmm) return nvec <= 8 ? 0 : nvec <= 16 ? 1 : 2;
+    return nvec <= 4 ? 0 : nvec <= 8 ? 1 : nvec <= 16 ? 2 : nvec <= 32 ? 3 : 4;
+}
 
 template <class EL, int LPN, int VPL, int U>
 __device__ __forceinline__ void spmm_rows(const SpmmProblem &P, int r0, int r1, int lane) {
@@ -51,21 +64,20 @@ __device__ __forceinline__ void spmm_rows(const SpmmProblem &P, int r0, int r1, 
     }
 }
 
-template <class EL>
-__device__ __forceinline__ void spmm_tile(const SpmmProblem &P, int r0, int r1, int lane) {
-    const int nvec = P.N / EL::V;
-    if (nvec <= 8)
-        spmm_rows<EL, 8, 1, 8>(P, r0, r1, lane);
-    else if (nvec <= 16)
-        spmm_rows<EL, 8, 2, 4>(P, r0, r1, lane);
-    else
-        spmm_rows<EL, 16, 2, 4>(P, r0, r1, lane);  // 32 vectors per column tile
-}
-
 template <class EL, int LPN, int VPL>
 __device__ __forceinline__ void sddmm_rows(const SddmmProblem &P, int r0, int r1, int lane) {
     using namespace sddmm_detail;
     const bool full = P.Kd == LPN * VPL * EL::V;
+    const int64_t e0 = __ldg(P.rowptr + r0), e1 = __ldg(P.rowptr + r1);
+    if (e1 - e0 < 32 * (int64_t)(r1 - r0)) {  // short rows: the tile's entries 32 at a time across rows
+        if (e1 > e0) {
+            if (full)
+                sddmm_entries<EL, LPN, VPL, false>(P, e0, e1, r0, lane);
+            else
+                sddmm_entries<EL, LPN, VPL, true>(P, e0, e1, r0, lane);
+        }
+        return;
+    }
     for (int row = r0; row < r1; ++row) {
         const int64_t p0 = __ldg(P.rowptr + row), p1 = __ldg(P.rowptr + row + 1);
         if (p0 == p1) continue;
@@ -76,22 +88,24 @@ __device__ __forceinline__ void sddmm_rows(const SddmmProblem &P, int r0, int r1
     }
 }
 
-template <class EL>
-__device__ __forceinline__ void sddmm_tile(const SddmmProblem &P, int r0, int r1, int lane) {
-    const int nvec = P.Kd / EL::V;  // at most 64 (checked on the host)
-    if (nvec <= 4)
-        sddmm_rows<EL, 4, 1>(P, r0, r1, lane);
-    else if (nvec <= 8)
-        sddmm_rows<EL, 4, 2>(P, r0, r1, lane);
-    else if (nvec <= 16)
-        sddmm_rows<EL, 8, 2>(P, r0, r1, lane);
-    else if (nvec <= 32)
-        sddmm_rows<EL, 16, 2>(P, r0, r1, lane);
-    else
-        sddmm_rows<EL, 32, 2>(P, r0, r1, lane);
+template <class EL, int KIND, int CLASS>
+__device__ __forceinline__ void run_tile(const GroupArgs &a, const Tile &t, int lane) {
+    if constexpr (KIND == kSpmm) {
+        const SpmmProblem &P = a.spmm[t.problem];
+        if constexpr (CLASS == 0) spmm_rows<EL, 8, 1, 8>(P, t.row0, t.row1, lane);
+        else if constexpr (CLASS == 1) spmm_rows<EL, 8, 2, 4>(P, t.row0, t.row1, lane);
+        else spmm_rows<EL, 16, 2, 4>(P, t.row0, t.row1, lane);  // 32 vectors per column tile
+    } else {
+        const SddmmProblem &P = a.sddmm[t.problem];
+        if constexpr (CLASS == 0) sddmm_rows<EL, 4, 1>(P, t.row0, t.row1, lane);
+        else if constexpr (CLASS == 1) sddmm_rows<EL, 8, 1>(P, t.row0, t.row1, lane);
+        else if constexpr (CLASS == 2) sddmm_rows<EL, 8, 2>(P, t.row0, t.row1, lane);
+        else if constexpr (CLASS == 3) sddmm_rows<EL, 16, 2>(P, t.row0, t.row1, lane);
+        else sddmm_rows<EL, 32, 2>(P, t.row0, t.row1, lane);
+    }
 }
 
-template <class EL, int KIND>
+template <class EL, int KIND, int CLASS>
 __global__ void __launch_bounds__(256) grouped_kernel(const GroupArgs a) {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -99,11 +113,7 @@ __global__ void __launch_bounds__(256) grouped_kernel(const GroupArgs a) {
         if (lane == 0) t = atomicAdd(a.ticket, 1u);
         t = __shfl_sync(FULL, t, 0);
         if (t >= (unsigned)a.ntiles) return;
-        const Tile tile = a.tiles[t];
-        if (KIND == kSpmm)
-            spmm_tile<EL>(a.spmm[tile.problem], tile.row0, tile.row1, lane);
-        else
-            sddmm_tile<EL>(a.sddmm[tile.problem], tile.row0, tile.row1, lane);
+        run_tile<EL, KIND, CLASS>(a, a.tiles[t], lane);
     }
 }
 
@@ -115,6 +125,8 @@ using namespace gbsp::batched;
 
 struct gbsp_batch_plan {
     int kind, dtype, G, ntiles;
+    int class_begin[kClasses + 1];  // tiles of layout class c: [class_begin[c], class_begin[c + 1])
+    int launches;
     int64_t nnz;
     SpmmProblem *d_spmm;
     SddmmProblem *d_sddmm;
@@ -160,18 +172,34 @@ int add_tiles(const gbsp_csr &A, int g, cudaStream_t s, std::vector<Tile> &tiles
     return GBSP_OK;
 }
 
+template <class EL, int KIND, int CLASS>
+void launch_class(gbsp_batch_plan *p, cudaStream_t cap) {
+    const int b = p->class_begin[CLASS], n = p->class_begin[CLASS + 1] - b;
+    if (n <= 0) return;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grouped_kernel<EL, KIND, CLASS>, 256, 0);
+    int nblocks = sm_count() * (per_sm < 1 ? 1 : per_sm);
+    if (nblocks > (n + 7) / 8) nblocks = (n + 7) / 8;  // no more warps than tiles
+    GroupArgs args{p->d_spmm, p->d_sddmm, p->d_tiles + b, n, p->d_ticket + CLASS};
+    grouped_kernel<EL, KIND, CLASS><<<nblocks, 256, 0, cap>>>(args);
+    ++p->launches;
+}
+
 template <class EL, int KIND>
 int record(gbsp_batch_plan *p) {
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grouped_kernel<EL, KIND>, 256, 0);
-    const int nblocks = sm_count() * (per_sm < 1 ? 1 : per_sm);
-    GroupArgs args{p->d_spmm, p->d_sddmm, p->d_tiles, p->ntiles, p->d_ticket};
     cudaStream_t cap = nullptr;
     if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return check_launch("batch stream");
     bool okc = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    p->launches = 0;
     if (okc) {
-        cudaMemsetAsync(p->d_ticket, 0, sizeof(unsigned), cap);
-        if (p->ntiles > 0) grouped_kernel<EL, KIND><<<nblocks, 256, 0, cap>>>(args);
+        cudaMemsetAsync(p->d_ticket, 0, sizeof(unsigned) * kClasses, cap);
+        launch_class<EL, KIND, 0>(p, cap);
+        launch_class<EL, KIND, 1>(p, cap);
+        launch_class<EL, KIND, 2>(p, cap);
+        if constexpr (KIND == kSddmm) {
+            launch_class<EL, KIND, 3>(p, cap);
+            launch_class<EL, KIND, 4>(p, cap);
+        }
         okc = cudaStreamEndCapture(cap, &p->graph) == cudaSuccess;
     }
     okc = okc && cudaGraphInstantiate(&p->exec, p->graph, 0) == cudaSuccess;
@@ -192,7 +220,7 @@ int create(int kind, int G, const gbsp_csr *A, const gbsp_dense *B, gbsp_dense *
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     std::vector<SpmmProblem> sp;
     std::vector<SddmmProblem> sd;
-    std::vector<Tile> tiles;
+    std::vector<Tile> by_class[kClasses];
     int64_t nnz = 0;
     const int dtype = kind == kSpmm ? (G > 0 ? B[0].dtype : GBSP_F32) : (G > 0 ? X[0].dtype : GBSP_F32);
     const int eb = elem_bytes(dtype);
@@ -249,20 +277,29 @@ int create(int kind, int G, const gbsp_csr *A, const gbsp_dense *B, gbsp_dense *
             p.dtype = dtype;
             sd.push_back(p);
         }
-        int st = add_tiles(a, g, s, tiles, nnz);
+        const int nvec = (int)((kind == kSpmm ? B[g].cols : X[g].cols) / V);
+        int st = add_tiles(a, g, s, by_class[layout_class(kind, nvec)], nnz);
         if (st) return st;
     }
+    std::vector<Tile> tiles;
+    int class_begin[kClasses + 1];
+    for (int c = 0; c < kClasses; ++c) {
+        class_begin[c] = (int)tiles.size();
+        tiles.insert(tiles.end(), by_class[c].begin(), by_class[c].end());
+    }
+    class_begin[kClasses] = (int)tiles.size();
     gbsp_batch_plan *p = new gbsp_batch_plan();
     p->kind = kind;
     p->dtype = dtype;
     p->G = G;
     p->ntiles = (int)tiles.size();
+    for (int c = 0; c <= kClasses; ++c) p->class_begin[c] = class_begin[c];
     p->nnz = nnz;
     const size_t nsp = sp.size(), nsd = sd.size();
     if (cudaMalloc(&p->d_spmm, sizeof(SpmmProblem) * (nsp ? nsp : 1)) != cudaSuccess ||
         cudaMalloc(&p->d_sddmm, sizeof(SddmmProblem) * (nsd ? nsd : 1)) != cudaSuccess ||
         cudaMalloc(&p->d_tiles, sizeof(Tile) * (tiles.empty() ? 1 : tiles.size())) != cudaSuccess ||
-        cudaMalloc(&p->d_ticket, sizeof(unsigned)) != cudaSuccess) {
+        cudaMalloc(&p->d_ticket, sizeof(unsigned) * kClasses) != cudaSuccess) {
         cudaGetLastError();
         batch_free(p);
         return fail(GBSP_ERR_OOM, "batch plan: allocation failed");
@@ -305,7 +342,7 @@ GBSP_EXPORT int gbsp_batch_plan_create_sddmm(int G, const gbsp_csr *S, const gbs
 GBSP_EXPORT int gbsp_batch_plan_execute(const gbsp_batch_plan *p, void *stream) {
     if (!p) return fail(GBSP_ERR_INVALID_ARG, "batch execute: null plan");
     if (cudaGraphLaunch(p->exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) return check_launch("batch execute");
-    if (p->ntiles > 0) count_launches(1);
+    count_launches(p->launches);
     return ok();
 }
 

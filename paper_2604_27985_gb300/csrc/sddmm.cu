@@ -6,6 +6,16 @@ namespace sddmm_detail {
 
 template <class EL, int LPN, int VPL>
 int run(const SddmmProblem &P, int variant, cudaStream_t s) {
+    if (variant == GBSP_VARIANT_ENTRY) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sddmm_entry_kernel<EL, LPN, VPL>, 256, 0) !=
+            cudaSuccess)
+            return check_launch("occupancy query");
+        const int nblocks = sm_count() * (per_sm < 1 ? 1 : per_sm);
+        sddmm_entry_kernel<EL, LPN, VPL><<<dim3(nblocks), 256, 0, s>>>(P, nblocks * 8);
+        count_launches(1);
+        return check_launch("sddmm entry split");
+    }
     if (variant == GBSP_VARIANT_MERGE) {
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sddmm_merge_kernel<EL, LPN, VPL>, 256, 0) !=

@@ -154,6 +154,178 @@ __global__ void __launch_bounds__(256) sddmm_merge_kernel(const SddmmProblem P, 
     }
 }
 
+// ---- entry split ------------------------------------------------------------------------
+//
+// For short or skewed rows: a warp takes a range of stored entries regardless of row
+// boundaries, 32 at a time, so no lane idles at the end of a short row and no warp waits
+// on a row's start.  Each chunk finds the row of every lane's entry from the row pointers
+// (one coalesced load of 32 row ends, then a 6-step binary search across the lanes by
+// shuffles), and a lane group reloads X_i only when the row of its entry changes.
+
+// Number of rows whose last entry precedes entry e (the row holding e): a 33-ary
+// warp-cooperative search over the row ends rowptr[1..M].
+__device__ __forceinline__ int row_of_entry(const int32_t *rowptr, int M, int64_t e, int lane) {
+    int64_t lo = 0, hi = M;  // the answer lies in [lo, hi]
+    while (hi - lo > 32) {
+        const int64_t span = hi - lo;
+        const int64_t probe = lo + (span * (lane + 1)) / 33;
+        const bool t = (int64_t)__ldg(rowptr + probe + 1) <= e;
+        const int k = __popc(__ballot_sync(FULL, t));
+        const int64_t new_lo = k == 0 ? lo : lo + (span * k) / 33 + 1;
+        const int64_t new_hi = k == 32 ? hi : lo + (span * (k + 1)) / 33;
+        lo = new_lo;
+        hi = new_hi;
+    }
+    const int64_t x = lo + lane;
+    const bool t = x < hi && (int64_t)__ldg(rowptr + x + 1) <= e;
+    return (int)(lo + __popc(__ballot_sync(FULL, t)));
+}
+
+// End of row rb + lane (rows past M end at "infinity"): one coalesced load of 32 row ends.
+__device__ __forceinline__ int64_t row_end(const int32_t *rowptr, int M, int rb, int lane) {
+    const int r = rb + 1 + lane;
+    return r <= M ? (int64_t)__ldg(rowptr + r) : INT64_MAX;
+}
+
+// The row of each lane's entry e, given that every lane's entry lies in row rc or later and
+// `end` holds row_end(rc) (loaded ahead by the caller).
+__device__ __forceinline__ int rows_of_chunk(const int32_t *rowptr, int M, int rc, int64_t end, int64_t e,
+                                             int lane) {
+    int row = -1;
+    for (int rb = rc;; rb += 32) {
+        if (rb != rc) end = row_end(rowptr, M, rb, lane);  // a run of more than 32 row ends
+        int lo = 0, len = 32;  // first k with end_k > e
+#pragma unroll
+        for (int it = 0; it < 6; ++it) {
+            const int half = len >> 1;
+            const int mid = lo + half;
+            const int64_t v = __shfl_sync(FULL, end, mid < 32 ? mid : 31);
+            const bool go = len > 0 && v <= e;
+            lo = go ? mid + 1 : lo;
+            len = len == 0 ? 0 : (go ? len - half - 1 : half);
+        }
+        if (row < 0 && lo < 32) row = rb + lo;
+        if (__all_sync(FULL, row >= 0)) return row;
+    }
+}
+
+// Entries [e0, e1), the first of which lies in row rc.  Per chunk: the column indices,
+// values and 32 row ends of the next chunk are loaded while this one computes; the Y rows
+// of U steps are gathered before any is used; a group fetches X_i only when its entry's
+// row differs from the one it holds.
+template <class EL, int LPN, int VPL, bool CHECK_COLS>
+__device__ __forceinline__ void sddmm_entries(const SddmmProblem &P, int64_t e0, int64_t e1, int rc, int lane) {
+    constexpr int U = LPN * VPL <= 8 ? LPN : (8 / VPL < 1 ? 1 : 8 / VPL);
+    const int sl = lane % LPN, g = lane / LPN;
+    using ST = typename EL::stored;
+    const ST *X = static_cast<const ST *>(P.X);
+    const uint4 *Yv = static_cast<const uint4 *>(P.Y) + sl;
+    const int64_t ldv = P.ldy / EL::V;
+    bool colok[VPL];
+    int k0[VPL];
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+        k0[v] = (v * LPN + sl) * EL::V;
+        colok[v] = !CHECK_COLS || k0[v] < P.Kd;
+    }
+    float x[VPL][EL::V];
+    int xrow = -1;
+
+    int c = 0;
+    float s = 0.f;
+    if (e0 + lane < e1) {
+        c = ld_stream(P.colidx + e0 + lane);
+        s = ld_stream(P.svals + e0 + lane);
+    }
+    int64_t end = row_end(P.rowptr, P.M, rc, lane);
+    for (int64_t base = e0; base < e1; base += 32) {
+        const int64_t nb = base + 32;
+        int c2 = 0;
+        float s2 = 0.f;
+        if (nb + lane < e1) {
+            c2 = ld_stream(P.colidx + nb + lane);
+            s2 = ld_stream(P.svals + nb + lane);
+        }
+        const int cnt = e1 - base < 32 ? (int)(e1 - base) : 32;
+        const int row = rows_of_chunk(P.rowptr, P.M, rc, end, lane < cnt ? base + lane : base, lane);
+        rc = __shfl_sync(FULL, row, cnt - 1);
+        if (nb < e1) end = row_end(P.rowptr, P.M, rc, lane);  // for the next chunk
+        float part[LPN];
+#pragma unroll
+        for (int t0 = 0; t0 < LPN; t0 += U) {
+            uint4 ry[U][VPL];
+            int rr[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int idx = g * LPN + t0 + u;
+                const int cj = __shfl_sync(FULL, c, idx);
+                rr[u] = __shfl_sync(FULL, row, idx);
+                const uint4 *rp = Yv + (int64_t)cj * ldv;
+#pragma unroll
+                for (int v = 0; v < VPL; ++v)
+                    ry[u][v] = idx < cnt && colok[v] ? ld_gather16(rp + v * LPN) : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (rr[u] != xrow) {  // this group's entry starts another row: fetch its X row
+                    xrow = rr[u];
+#pragma unroll
+                    for (int v = 0; v < VPL; ++v) {
+                        uint4 raw = make_uint4(0, 0, 0, 0);
+                        if (colok[v]) raw = ld_gather16(X + (int64_t)xrow * P.ldx + k0[v]);
+                        EL::unpack(raw, x[v]);
+                    }
+                }
+                float sum = 0.f;
+#pragma unroll
+                for (int v = 0; v < VPL; ++v) {
+                    float y[EL::V];
+                    EL::unpack(ry[u][v], y);
+#pragma unroll
+                    for (int k = 0; k < EL::V; ++k) sum = fmaf(x[v][k], y[k], sum);
+                }
+                part[t0 + u] = sum;
+            }
+        }
+#pragma unroll
+        for (int h = LPN / 2; h >= 1; h >>= 1) {
+            const bool upper = (sl & h) != 0;
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const float send = upper ? part[i] : part[i + h];
+                const float keep = upper ? part[i + h] : part[i];
+                part[i] = keep + __shfl_xor_sync(FULL, send, h);
+            }
+        }
+        if (lane < cnt) {
+            float r = s * part[0];
+            if (EL::dtype == GBSP_E4M3) r *= __ldg(P.x_scale + row) * __ldg(P.y_scale + c);
+            __stcs(P.out + base + lane, r);
+        }
+        c = c2;
+        s = s2;
+    }
+}
+
+// Stored entries split evenly across the nwarps warps of the grid, in whole chunks of 32
+// (nnz is read on the device, so the launch needs no host-side statistics).
+template <class EL, int LPN, int VPL>
+__global__ void __launch_bounds__(256) sddmm_entry_kernel(const SddmmProblem P, int nwarps) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t rnnz = __ldg(P.rowptr + P.M);
+    const int64_t nnz = P.nnz >= 0 && P.nnz < rnnz ? P.nnz : rnnz;
+    const int64_t chunks_per_warp = ((nnz + 31) / 32 + nwarps - 1) / nwarps;
+    const int64_t e0 = min(w * chunks_per_warp * 32, nnz);
+    const int64_t e1 = min(e0 + chunks_per_warp * 32, nnz);
+    if (e0 >= e1) return;
+    const int rc = row_of_entry(P.rowptr, P.M, e0, lane);
+    if (P.Kd == LPN * VPL * EL::V)
+        sddmm_entries<EL, LPN, VPL, false>(P, e0, e1, rc, lane);
+    else
+        sddmm_entries<EL, LPN, VPL, true>(P, e0, e1, rc, lane);
+}
+
 // Any Kd and alignment: one lane per stored entry, plain loads.  X_i is read by all lanes
 // of the warp at the same address (a broadcast).  Suits small Kd such as the paper's D = 2.
 template <class EL>

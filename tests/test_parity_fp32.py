@@ -189,11 +189,11 @@ def run_sddmm(gb, S, X, Y, **kw):
 
 @pytest.mark.parametrize("name", list(MATS))
 @pytest.mark.parametrize("Kd", [2, 4, 8, 16, 32, 36, 64, 128, 256, 512, 33])
-@pytest.mark.parametrize("variant", ["auto", "merge"])
+@pytest.mark.parametrize("variant", ["auto", "merge", "entry"])
 def test_sddmm_fp32(gb, name, Kd, variant):
     S = mat(name)
     X, Y = gen.dense_normal(S.M, Kd, 41), gen.dense_normal(S.K, Kd, 42)
-    if variant == "merge" and Kd % 4:
+    if variant != "auto" and Kd % 4:
         with pytest.raises(gb.GbspError, match="ALIGN"):
             run_sddmm(gb, S, X, Y, variant=variant)
         return
@@ -204,13 +204,57 @@ def test_sddmm_fp32(gb, name, Kd, variant):
 
 @pytest.mark.parametrize("vecs", [1, 2, 4])
 @pytest.mark.parametrize("Kd", [8, 32, 40, 128, 256, 512])
-@pytest.mark.parametrize("variant", ["rowsplit", "merge"])
+@pytest.mark.parametrize("variant", ["rowsplit", "merge", "entry"])
 def test_sddmm_layouts(gb, vecs, Kd, variant):
     S = mat("powerlaw")
     X, Y = gen.dense_normal(S.M, Kd, 51), gen.dense_normal(S.K, Kd, 52)
     out = run_sddmm(gb, S, X, Y, vecs=vecs, variant=variant)
     ref, scale = oracle.sddmm(S.rowptr, S.colidx, S.vals, X, Y)
     assert_within(out, ref, scale, TOL, f"vecs={vecs} Kd={Kd}")
+
+
+def _entry_edge_cases():
+    """Row-length patterns that stress the entry split's row search: runs of empty rows longer
+    than a 32-entry chunk's 32 row ends, single-entry rows, rows of 31 / 32 / 33 entries,
+    a long row, and empty rows at both ends."""
+    rng = np.random.default_rng(61)
+    lengths = np.concatenate([
+        np.zeros(70, np.int64), np.ones(100, np.int64), np.zeros(40, np.int64), [31, 32, 33, 1, 0, 64],
+        np.zeros(200, np.int64), rng.integers(0, 5, 300), [900], rng.integers(0, 3, 500), np.zeros(37, np.int64)])
+    return gen.csr_from_lengths(lengths, 1000, seed=62)
+
+
+@pytest.mark.parametrize("Kd", [4, 32, 64, 132, 512])
+@pytest.mark.parametrize("variant", ["entry", "auto"])
+def test_sddmm_entry_split_edge_cases(gb, Kd, variant):
+    S = _entry_edge_cases()
+    assert S.nnz < 32 * S.M  # auto takes the entry split here
+    X, Y = gen.dense_normal(S.M, Kd, 63), gen.dense_normal(S.K, Kd, 64)
+    out = run_sddmm(gb, S, X, Y, variant=variant)
+    ref, scale = oracle.sddmm(S.rowptr, S.colidx, S.vals, X, Y)
+    assert_within(out, ref, scale, TOL, f"entry split Kd={Kd}")
+
+
+@pytest.mark.parametrize("nnz", [0, 1, 5, 31, 32, 33])
+def test_sddmm_entry_split_tiny(gb, nnz):
+    import torch
+
+    rng = np.random.default_rng(nnz)
+    lengths = np.zeros(50, np.int64)
+    lengths[rng.choice(50, nnz, replace=True)] += 1 if nnz else 0
+    S = gen.csr_from_lengths(lengths, 60, seed=65)
+    X, Y = gen.dense_int(S.M, 32, 66), gen.dense_int(S.K, 32, 67)
+    out = gb.sddmm(dev(S.rowptr), dev(S.colidx), dev(S.vals) if S.nnz else torch.zeros(1, device="cuda"), dev(X),
+                   dev(Y), out=torch.full((max(S.nnz, 1),), np.nan, device="cuda"), variant="entry").cpu().numpy()
+    ref, scale = oracle.sddmm(S.rowptr, S.colidx, S.vals, X, Y)
+    if S.nnz:
+        assert_within(out[:S.nnz], ref, scale, TOL, f"entry split nnz={nnz}")
+
+
+def test_spmm_rejects_entry_split(gb):
+    A = mat("ragged")
+    with pytest.raises(gb.GbspError, match="UNSUPPORTED"):
+        run_spmm(gb, A, gen.dense_normal(A.K, 8, 68), variant="entry")
 
 
 @pytest.mark.parametrize("Kd", [8, 32, 128])

@@ -158,7 +158,7 @@ def test_spmm_lowp_integers_bit_exact(gb, variant):
 # ---- SDDMM -----------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("Kd", [32, 128, 256, 40])
-@pytest.mark.parametrize("variant", ["rowsplit", "merge"])
+@pytest.mark.parametrize("variant", ["rowsplit", "merge", "entry"])
 def test_sddmm_bf16(gb, Kd, variant):
     S = mat("uniform")
     X, Y = gen.dense_normal(S.M, Kd, 21), gen.dense_normal(S.K, Kd, 22)
@@ -172,7 +172,7 @@ def test_sddmm_bf16(gb, Kd, variant):
 
 
 @pytest.mark.parametrize("Kd", [32, 128, 256, 48])
-@pytest.mark.parametrize("variant", ["rowsplit", "merge"])
+@pytest.mark.parametrize("variant", ["rowsplit", "merge", "entry"])
 def test_sddmm_e4m3(gb, Kd, variant):
     S = mat("clustered")
     X, Y = gen.dense_normal(S.M, Kd, 23), gen.dense_normal(S.K, Kd, 24)
@@ -207,6 +207,8 @@ def test_sddmm_lowp_integers_bit_exact(gb):
     out = gb.sddmm(dev(S.rowptr), dev(S.colidx), dev(svals), dev(oracle.bf16_round(X).view(np.int16)).view(torch.bfloat16),
                    dev(oracle.bf16_round(Y).view(np.int16)).view(torch.bfloat16)).cpu().numpy()
     assert np.array_equal(out.astype(np.float64), want)
-    out = gb.sddmm(dev(S.rowptr), dev(S.colidx), dev(svals), dev(oracle.e4m3_round(X)), dev(oracle.e4m3_round(Y)),
-                   x_scale=dev(np.ones(S.M, np.float32)), y_scale=dev(np.ones(S.K, np.float32))).cpu().numpy()
-    assert np.array_equal(out.astype(np.float64), want)
+    for variant in ("auto", "entry"):
+        out = gb.sddmm(dev(S.rowptr), dev(S.colidx), dev(svals), dev(oracle.e4m3_round(X)), dev(oracle.e4m3_round(Y)),
+                       x_scale=dev(np.ones(S.M, np.float32)), y_scale=dev(np.ones(S.K, np.float32)),
+                       variant=variant).cpu().numpy()
+        assert np.array_equal(out.astype(np.float64), want)
