@@ -193,7 +193,8 @@ struct TcShape {
     static constexpr int SMEM = S * STAGE + 1024 + 256;     // + alignment slack + barriers
 };
 
-constexpr int kTcThreads = 128;  // 4 warps: warp 0 lane 0 loads, warp 1 lane 0 issues MMAs, all 4 read TMEM
+constexpr int kTcThreads = 128;  // 4 warps: warp 0 loads, warp 1 lane 0 issues MMAs, all 4 read TMEM
+constexpr int kIssuers = 16;     // lanes of warp 0 that issue the TMA copies
 
 template <int NT, bool FP8>
 __global__ void __launch_bounds__(kTcThreads) tc_window_kernel(const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
@@ -231,23 +232,32 @@ __global__ void __launch_bounds__(kTcThreads) tc_window_kernel(const __grid_cons
     const uint32_t taddr = *tslot;
 
     // Warp 0 produces (TMA), warp 1 issues the MMAs; each runs ahead as far as the stages
-    // allow.  (Gathering the rows with 16-byte copies from four producer warps instead
-    // measured 1.9x slower than one TMA copy per block.)
-    if (tid == 0) {
+    // allow.  Four lanes of warp 0 issue a stage's block copies between them (lane 0 first
+    // arms the stage's barrier and copies the value tile); their barrier waits are decided
+    // together so the four stay in step.  (Gathering the rows with 16-byte copies from four
+    // producer warps instead measured 1.9x slower than one TMA copy per block.)
+    if (warp == 0 && lane < kIssuers) {
+        constexpr unsigned kMask = (1u << kIssuers) - 1u;
         bool ok = true;
         int issued = 0;
         for (int ch = 0; ch < nch; ++ch) {
             const int s = ch % SH::S;
-            if (ch >= SH::S && !mbar_wait(&empty[s], ((ch / SH::S) - 1) & 1)) {  // stage's MMAs done
-                ok = false;
-                break;
+            if (ch >= SH::S) {  // stage's MMAs done
+                const bool got = mbar_wait(&empty[s], ((ch / SH::S) - 1) & 1);
+                if (!__all_sync(kMask, got)) {
+                    ok = false;
+                    break;
+                }
             }
             uint8_t *bt = smem + s * SH::STAGE;
             if (ch == a.withhold && blockIdx.x == 0) continue;  // nothing will complete full[s]
-            mbar_expect_tx(&full[s], SH::STAGE);
-            bulk_load(bt + SH::BT, a.atiles + (size_t)(b0 / SH::BPS + ch) * kATile, kATile, &full[s]);
+            if (lane == 0) {
+                mbar_expect_tx(&full[s], SH::STAGE);
+                bulk_load(bt + SH::BT, a.atiles + (size_t)(b0 / SH::BPS + ch) * kATile, kATile, &full[s]);
+            }
+            __syncwarp(kMask);
 #pragma unroll 1
-            for (int kb = 0; kb < SH::BPS; ++kb) {
+            for (int kb = lane; kb < SH::BPS; kb += kIssuers) {
                 const int q = ch * SH::BPS + kb;
                 const int col = q < kStagedCols ? s_cols[q] : a.blk_col[b0 + q];
                 const int y = col >= 0 ? col * kBC : a.K;  // padding block: rows past K read as zeros
@@ -261,10 +271,11 @@ __global__ void __launch_bounds__(kTcThreads) tc_window_kernel(const __grid_cons
             }
             issued = ch + 1;
         }
-        if (!ok) atomicExch(a.err, 1);
+        if (!ok && lane == 0) atomicExch(a.err, 1);
         // every issued copy lands before the CTA can leave (bounded waits)
-        for (int ch = issued - SH::S > 0 ? issued - SH::S : 0; ch < issued; ++ch)
-            mbar_wait(&full[ch % SH::S], (ch / SH::S) & 1);
+        if (lane == 0)
+            for (int ch = issued - SH::S > 0 ? issued - SH::S : 0; ch < issued; ++ch)
+                mbar_wait(&full[ch % SH::S], (ch / SH::S) & 1);
     } else if (tid == 32) {
         bool ok = true;
         for (int i = 0; i < nch; ++i) {
