@@ -188,7 +188,7 @@ struct TcShape {
     static constexpr int NFA = FP8 ? NT : 2 * NT;           // 128-byte feature atoms per 8-row group
     static constexpr int BT = BPS * NFA * 1024;             // gathered B bytes per stage
     static constexpr int STAGE = BT + kATile;               // bytes per stage
-    static constexpr int S = NT <= 2 ? 3 : 2;                  // pipeline depth (2 CTAs per SM for NT <= 2)
+    static constexpr int S = 1;  // one stage per CTA: 5 CTAs per SM (NT <= 2) overlap better than deeper pipelines in fewer CTAs
     static constexpr int NCOLS = NT <= 2 ? 32 : 64;         // TMEM columns (16 per feature tile)
     static constexpr int SMEM = S * STAGE + 1024 + 256;     // + alignment slack + barriers
 };
