@@ -105,6 +105,29 @@ __device__ __forceinline__ float ld_stream(const float *p) { return __ldcs(p); }
 __device__ __forceinline__ uint16_t ld_stream(const uint16_t *p) { return __ldcs(reinterpret_cast<const unsigned short *>(p)); }
 __device__ __forceinline__ uint8_t ld_stream(const uint8_t *p) { return __ldcs(reinterpret_cast<const unsigned char *>(p)); }
 
+// Packed FP32 arithmetic (FFMA2 on sm_100+): two independent single-rounding fmas per
+// instruction.  axpy2 gives every element exactly what fmaf gives it; dot2 keeps two
+// running sums (even and odd elements), added at the end.  Used where instruction issue
+// binds (the graph chain, the entry-split SDDMM on short rows); measured on the same GPU,
+// the L2-bound row-split SpMM / SDDMM kernels ran 5-14% slower with it at N = Kd = 256, so
+// they keep scalar fmaf.
+template <int V>
+__device__ __forceinline__ void axpy2(float a, const float (&b)[V], float (&acc)[V]) {
+    static_assert(V % 2 == 0, "pairs");
+#pragma unroll
+    for (int k = 0; k < V; k += 2) {
+        const float2 r = __ffma2_rn(make_float2(a, a), make_float2(b[k], b[k + 1]), make_float2(acc[k], acc[k + 1]));
+        acc[k] = r.x;
+        acc[k + 1] = r.y;
+    }
+}
+template <int V>
+__device__ __forceinline__ void dot2(const float (&x)[V], const float (&y)[V], float2 &acc) {
+    static_assert(V % 2 == 0, "pairs");
+#pragma unroll
+    for (int k = 0; k < V; k += 2) acc = __ffma2_rn(make_float2(x[k], x[k + 1]), make_float2(y[k], y[k + 1]), acc);
+}
+
 // Gathered dense rows: read-only path, 16 bytes per lane.  (Skipping L1 allocation for
 // them measured 1-9% slower on the 65,536^2 and 16,384^2 workloads, so they stay cached.)
 __device__ __forceinline__ uint4 ld_gather16(const void *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }

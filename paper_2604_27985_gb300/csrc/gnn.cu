@@ -65,21 +65,19 @@ __device__ __forceinline__ void gnn_step(const uint4 *Hv, int64_t ldv, const boo
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         float f[VPL][8];
-        float dot = 0.f;
+        float2 d2 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int v = 0; v < VPL; ++v) {
             BF16::unpack(raw[u][v], f[v]);
-#pragma unroll
-            for (int t = 0; t < 8; ++t) dot = fmaf(x[v][t], f[v][t], dot);
+            dot2(x[v], f[v], d2);
         }
+        float dot = d2.x + d2.y;
 #pragma unroll
         for (int off = LPN / 2; off >= 1; off >>= 1) dot += __shfl_xor_sync(FULL, dot, off);
         const float e = sj[u] * dot;
         if (sl == 0 && ok[u]) E[base + q + u * G + sub] = e;
 #pragma unroll
-        for (int v = 0; v < VPL; ++v)
-#pragma unroll
-            for (int t = 0; t < 8; ++t) acc[v][t] = fmaf(e, f[v][t], acc[v][t]);
+        for (int v = 0; v < VPL; ++v) axpy2(e, f[v], acc[v]);
     }
 }
 

@@ -276,15 +276,14 @@ __device__ __forceinline__ void sddmm_entries(const SddmmProblem &P, int64_t e0,
                         EL::unpack(raw, x[v]);
                     }
                 }
-                float sum = 0.f;
+                float2 sum = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int v = 0; v < VPL; ++v) {
                     float y[EL::V];
                     EL::unpack(ry[u][v], y);
-#pragma unroll
-                    for (int k = 0; k < EL::V; ++k) sum = fmaf(x[v][k], y[k], sum);
+                    dot2(x[v], y, sum);
                 }
-                part[t0 + u] = sum;
+                part[t0 + u] = sum.x + sum.y;
             }
         }
 #pragma unroll
