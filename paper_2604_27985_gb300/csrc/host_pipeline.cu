@@ -13,6 +13,7 @@
 // them with the matrix's absolute entry numbers, so the kernels get base pointers moved
 // back by rowptr[r0].
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "common.cuh"
@@ -98,10 +99,13 @@ GBSP_EXPORT int gbsp_spmm_sddmm_host(const int32_t *rowptr, const int32_t *colid
     if (slots < 2) slots = 2;
     if (slots > chunks) slots = chunks;
     cudaStream_t user = static_cast<cudaStream_t>(stream);
-    // chunk boundaries with about equal entries
+    // chunk boundaries: the first c chunks hold a fraction 1 - (1 - c / chunks)^1.5 of the
+    // entries, so chunks shrink toward the end and the last chunk's compute and copy-back,
+    // which nothing overlaps, stay short
     std::vector<int64_t> bounds(1, 0);
     for (int c = 1; c < chunks; ++c) {
-        const int64_t want = nnz * c / chunks;
+        const double rest = 1.0 - (double)c / chunks;
+        const int64_t want = (int64_t)((double)nnz * (1.0 - rest * std::sqrt(rest)));
         int64_t lo = bounds.back() + 1, hi = M - (chunks - c);
         while (lo < hi) {  // first row whose start reaches `want`
             const int64_t mid = (lo + hi) / 2;
