@@ -161,8 +161,8 @@ int gbsp_spmm_sddmm_host(const int32_t *rowptr, const int32_t *colidx, const flo
 /* ---- condensed-tile tensor-core plan (BF16, E4M3) ----------------------------------------- */
 
 /* A plan splits a BF16 or per-row-scaled E4M3 CSR matrix A into dense 16 x 8 blocks
- * (aligned; at least `threshold` stored entries, default 16 when threshold < 1) and a
- * residual CSR.  Executing it computes C = A B (Eq. 1) as: residual SpMM through the CSR
+ * (aligned; at least `threshold` stored entries; when threshold < 1, 14 for BF16 and 10 for
+ * E4M3) and a residual CSR.  Executing it computes C = A B (Eq. 1) as: residual SpMM through the CSR
  * kernels (which writes C), then, for each 16-row window holding dense blocks, a tcgen05 MMA
  * of the window's condensed 16 x Kc tile with the Kc gathered rows of B (FP32 accumulation
  * in tensor memory), added into C.  The plan keeps its own device copy of everything it

@@ -671,7 +671,9 @@ GBSP_EXPORT int gbsp_plan_create(const gbsp_csr *A, int32_t threshold, const gbs
         return fail(GBSP_ERR_INVALID_ARG, "plan: E4M3 values need row scales");
     if (A->rows > 0 && !A->rowptr) return fail(GBSP_ERR_INVALID_ARG, "plan: null rowptr");
     if (A->nnz > 0 && (!A->colidx || !A->vals)) return fail(GBSP_ERR_INVALID_ARG, "plan: null colidx / vals");
-    if (threshold < 1) threshold = 16;
+    // defaults measured on 16,384^2 at 90% (N = 256), uniform and clustered: the E4M3 residual
+    // runs on ALU-bound CSR kernels, so sparser blocks still pay on the tensor cores
+    if (threshold < 1) threshold = A->dtype == GBSP_E4M3 ? 10 : 14;
     const int64_t M = A->rows, K = A->cols;
     const int64_t nwin = (M + kBR - 1) / kBR, nbc = (K + kBC - 1) / kBC;
     if (nwin * nbc > (int64_t)1 << 28)

@@ -36,7 +36,7 @@ def plan_of(gb, A, vals, threshold=0):
 @pytest.mark.parametrize("threshold", [0, 1, 40, 129])
 @pytest.mark.parametrize("N", [128, 256])
 def test_tc_integers_bit_exact(gb, threshold, N):
-    """threshold 1: every occupied block on the tensor cores; 129: none; 0 (default 16) and
+    """threshold 1: every occupied block on the tensor cores; 129: none; 0 (default 14) and
     40: the clustered blocks on the tensor cores, the scattered rest on the CSR kernels."""
     A = gen.csr_clustered(1024, 1024, 0.9, seed=401)
     vals = gen.vals_int(A.nnz, 402)

@@ -43,7 +43,7 @@ def effective_values(rowptr, colidx, K, qa, sa, tb, threshold):
     eff = s32[rows].astype(np.float64) * deq * t32[ci].astype(np.float64)
     key = (rows // 16) * ((K + 7) // 8) + ci // 8
     _, inv, cnt = np.unique(key, return_inverse=True, return_counts=True)
-    dense = cnt[inv] >= (threshold if threshold >= 1 else 16)
+    dense = cnt[inv] >= (threshold if threshold >= 1 else 10)  # the E4M3 default
     at = (s32[rows] * deq.astype(np.float32)).astype(np.float32) * t32[ci]
     amax = np.zeros(M, np.float32)
     np.maximum.at(amax, rows[dense], np.abs(at[dense]))
