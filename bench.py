@@ -439,7 +439,8 @@ def _line(metric, value, unit, ms, args, dtype, config, **extra):
 
 def run_precision(args):
     """16,384^2 at 90%, N = Kd = 256: SpMM + SDDMM in FP32, BF16, E4M3 (CUDA cores) and the
-    BF16 / E4M3 condensed-tile tensor-core plans, on the uniform and the clustered layouts."""
+    BF16 / E4M3 condensed-tile tensor-core plans (SpMM and SDDMM), on the uniform and the
+    clustered layouts."""
     import torch
 
     import paper_2604_27985_gb300 as gb
@@ -470,9 +471,9 @@ def run_precision(args):
             "bf16": (lambda: gb.spmm(rp, ci, qa, qb, out=C), lambda: gb.sddmm(rp, ci, v, qx, qy, out=out), 2, 2),
             "e4m3": (lambda: gb.spmm(rp, ci, ea, eb, out=C, a_scale=sa, b_scale=sb),
                      lambda: gb.sddmm(rp, ci, v, ex, ey, out=out, x_scale=ux, y_scale=uy), 1, 1),
-            "tc_bf16": (lambda: plan.execute(qb, out=C), lambda: gb.sddmm(rp, ci, v, qx, qy, out=out), 2, 2),
+            "tc_bf16": (lambda: plan.execute(qb, out=C), lambda: plan.sddmm(v, qx, qy, out=out), 2, 2),
             "tc_e4m3": (lambda: plan8.execute(eb, out=C, row_scale=sb),
-                        lambda: gb.sddmm(rp, ci, v, ex, ey, out=out, x_scale=ux, y_scale=uy), 1, 1),
+                        lambda: plan8.sddmm(v, ex, ey, out=out, x_scale=ux, y_scale=uy), 1, 1),
         }
         for name, (f_spmm, f_sddmm, vb, eb_) in runs.items():
             ms_a = _event_ms(f_spmm, args.steps, args.warmup, stream)

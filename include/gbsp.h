@@ -189,6 +189,20 @@ typedef struct gbsp_plan gbsp_plan;
 int gbsp_plan_create(const gbsp_csr *A, int32_t threshold, const gbsp_opts *residual_opts, void *stream,
                      gbsp_plan **out);
 int gbsp_plan_execute(const gbsp_plan *plan, const gbsp_dense *B, gbsp_dense *C, void *stream);
+/* SDDMM on the plan's sparsity pattern (Eq. 2): out[p] = svals[p] * <X_i, Y_j> for every
+ * stored entry p = (i, j) of the matrix the plan was made from, in that matrix's CSR order
+ * (svals and out: device float[nnz]; the plan's own values are not used).  X (M x Kd) and
+ * Y (K x Kd) both BF16, or both E4M3 with row scales (X->row_scale u_i, Y->row_scale v_j;
+ * the result is scaled by u_i v_j).  Residual entries run on the row-split CSR kernel; the
+ * 16 x 8 outputs of each dense block come from one tcgen05 MMA per 16 blocks and K-step:
+ * D (128 x 16) = Y_g X_w^T with the blocks' Y rows and the window's X rows in shared
+ * memory (TMA), FP32 accumulation in tensor memory, and the epilogue writes the stored
+ * entries only.  Requirements: Kd and both leading dimensions multiples of 16 bytes' worth
+ * of elements, 16-byte aligned X and Y, Kd <= 512 (GBSP_ERR_ALIGN otherwise); when any
+ * window is dense, Kd a multiple of 64 (BF16) or 128 (E4M3) (GBSP_ERR_UNSUPPORTED).
+ * Asynchronous; waits are bounded as in gbsp_plan_execute (see gbsp_plan_check). */
+int gbsp_plan_sddmm(const gbsp_plan *plan, const float *svals, const gbsp_dense *X, const gbsp_dense *Y, float *out,
+                    void *stream);
 int gbsp_plan_info(const gbsp_plan *plan, int64_t *info, int n);
 int gbsp_plan_check(const gbsp_plan *plan, void *stream);
 /* Testing the timeout path (no counterpart in the paper): while chunk >= 0, the first

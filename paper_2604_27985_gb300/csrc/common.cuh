@@ -183,6 +183,7 @@ struct SddmmProblem {
     const float *y_scale;
     float *out;
     int dtype;  // dtype of X and Y
+    const int32_t *pos;  // row split only: entry e's value and output at pos[e] (null: at e)
 };
 
 // SpMM launchers: one translation unit per (element type, algorithm).

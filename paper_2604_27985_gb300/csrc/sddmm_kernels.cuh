@@ -52,7 +52,9 @@ __device__ __forceinline__ void sddmm_chunk(const uint4 *__restrict__ Yv, int64_
 }
 
 // Entries [p0, p1) of row `row`: X_i in registers, entries 32 at a time with the next 32
-// column indices and values prefetched while the current ones are used.
+// column indices and values prefetched while the current ones are used.  With P.pos, entry
+// e's value and output sit at position P.pos[e] of the caller's arrays (a sub-matrix of
+// another CSR, such as the residual of a tensor-core plan).
 template <class EL, int LPN, int VPL, bool CHECK_COLS>
 __device__ __forceinline__ void sddmm_segment(const SddmmProblem &P, int row, int64_t p0, int64_t p1, int lane) {
     const int sl = lane % LPN, g = lane / LPN;
@@ -75,17 +77,21 @@ __device__ __forceinline__ void sddmm_segment(const SddmmProblem &P, int row, in
 
     int c = 0;
     float s = 0.f;
+    int64_t q = p0 + lane;  // where this lane's entry keeps its value and output
     if (p0 + lane < p1) {
         c = ld_stream(P.colidx + p0 + lane);
-        s = ld_stream(P.svals + p0 + lane);
+        if (P.pos) q = __ldg(P.pos + p0 + lane);
+        s = ld_stream(P.svals + q);
     }
     for (int64_t base = p0; base < p1; base += 32) {
         const int64_t nb = base + 32;
         int c2 = 0;
         float s2 = 0.f;
+        int64_t q2 = nb + lane;
         if (nb + lane < p1) {
             c2 = ld_stream(P.colidx + nb + lane);
-            s2 = ld_stream(P.svals + nb + lane);
+            if (P.pos) q2 = __ldg(P.pos + nb + lane);
+            s2 = ld_stream(P.svals + q2);
         }
         float part[LPN];
         if (nb <= p1)
@@ -105,9 +111,10 @@ __device__ __forceinline__ void sddmm_segment(const SddmmProblem &P, int row, in
         if (base + lane < p1) {
             float r = s * part[0];
             if (EL::dtype == GBSP_E4M3) r *= xs * __ldg(P.y_scale + c);
-            __stcs(P.out + base + lane, r);
+            __stcs(P.out + q, r);
         }
         c = c2;
+        q = q2;
         s = s2;
     }
 }

@@ -56,6 +56,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -421,10 +425,13 @@ __device__ __forceinline__ int atile_offset(int r, int b) {
 
 // Scatters the entries of dense blocks into the swizzled value tiles (BF16 values, or the
 // E4M3 codes that each execution folds with B's row scales and requantises) and counts the
-// rest per row.
+// rest per row.  For the SDDMM it also records, per dense block and block row, the CSR
+// position of the row's first entry in the block (bstart) and which of the 8 columns are
+// stored (bmask; a row's entries in one block are consecutive in CSR order).
 template <bool FP8>
 __global__ void fill_values_kernel(const int32_t *rowptr, const int32_t *colidx, const void *vals, int M, int nbc,
-                                   const int32_t *slot, const int32_t *win_off, uint8_t *tiles, int32_t *res_len) {
+                                   const int32_t *slot, const int32_t *win_off, uint8_t *tiles, int32_t *res_len,
+                                   int32_t *bstart, uint32_t *bmask) {
     const int lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= M) return;
@@ -438,6 +445,8 @@ __global__ void fill_values_kernel(const int32_t *rowptr, const int32_t *colidx,
         const int sl = s[col / kBC];
         if (sl >= 0) {
             const int blk = off + sl;
+            atomicOr(bmask + (int64_t)blk * kBR + r, 1u << (col % kBC));
+            if (p == p0 || colidx[p - 1] / kBC != col / kBC) bstart[(int64_t)blk * kBR + r] = (int32_t)p;
             if constexpr (FP8) {
                 const int k = (blk % 16) * kBC + col % kBC;
                 tiles[(int64_t)(blk / 16) * kATile + atile_offset(r, k)] = static_cast<const uint8_t *>(vals)[p];
@@ -454,10 +463,12 @@ __global__ void fill_values_kernel(const int32_t *rowptr, const int32_t *colidx,
     if (lane == 0) res_len[row] = resid;
 }
 
-// Copies the residual entries of each row, in order, to the residual CSR.
+// Copies the residual entries of each row, in order, to the residual CSR, with each one's
+// position in A's CSR (for the SDDMM, whose values and outputs are in that order).
 template <typename T>
 __global__ void fill_residual_kernel(const int32_t *rowptr, const int32_t *colidx, const T *vals, int M, int nbc,
-                                     const int32_t *slot, const int32_t *res_ptr, int32_t *res_col, T *res_val) {
+                                     const int32_t *slot, const int32_t *res_ptr, int32_t *res_col, T *res_val,
+                                     int32_t *res_pos) {
     const int lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= M) return;
@@ -477,6 +488,7 @@ __global__ void fill_residual_kernel(const int32_t *rowptr, const int32_t *colid
             const int64_t q = out + __popc(bal & ((1u << lane) - 1u));
             res_col[q] = col;
             res_val[q] = vals[p];
+            res_pos[q] = (int32_t)p;
         }
         out += __popc(bal);
     }
@@ -561,6 +573,175 @@ __global__ void __launch_bounds__(256) fold_e4m3_kernel(const uint8_t *__restric
     }
 }
 
+// ---- condensed-tile SDDMM ------------------------------------------------------------------
+//
+// For a window with dense blocks, the 16 x 8 outputs of each block are one small product:
+//   D (128 x 16) = Y_g (128 x Kd) X_w^T (Kd x 16)
+// with Y_g the Y rows of 16 blocks' columns (8 each) and X_w the window's 16 X rows, both
+// K-major (Kd contiguous) in 128-byte-swizzled shared memory; the epilogue writes
+// out[p] = s_p D[j][i] only for the stored entries (Eq. 2), found from the plan's per block
+// row first position and column mask.  One stage of 16 blocks at a time; two TMEM buffers
+// let stage ch's epilogue overlap stage ch + 1's copies and MMAs.
+
+constexpr int kSdBlocks = 16;  // dense blocks per stage: MMA M = 128 gathered Y rows
+
+struct TcSddmmArgs {
+    const int32_t *win_row0, *win_blk, *blk_col;
+    const int32_t *bstart;
+    const uint32_t *bmask;
+    const float *svals;
+    float *out;
+    const float *x_scale, *y_scale;  // E4M3 per-row scales of X and Y, else null
+    int M, Ny, KB;                   // rows of X and of Y; 128-byte K-blocks per row
+    int *err;
+};
+
+template <bool FP8>
+__global__ void __launch_bounds__(128) tc_sddmm_kernel(const __grid_constant__ CUtensorMap tmY,
+                                                       const __grid_constant__ CUtensorMap tmX,
+                                                       const TcSddmmArgs a) {
+    constexpr uint32_t kIdesc = (1u << 4) | ((FP8 ? 0u : 1u) << 7) | ((FP8 ? 0u : 1u) << 10) | ((16u >> 3) << 17) |
+                                ((128u >> 4) << 24);  // FP32 D, both operands K-major, M = 128, N = 16
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int KB = a.KB;
+    uint8_t *stage = smem;                              // [16 blocks][KB][8 rows][128 B]
+    uint8_t *xt = smem + kSdBlocks * KB * 1024;         // [KB][16 rows][128 B]
+    uint64_t *full = reinterpret_cast<uint64_t *>(xt + 2 * KB * 1024);
+    uint64_t *xfull = full + 1;
+    uint64_t *mdone = full + 2;     // [2]
+    uint64_t *epi_done = full + 4;  // [2]
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(full + 6);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int w = blockIdx.x;
+    const int b0 = a.win_blk[w], b1 = a.win_blk[w + 1];
+    const int nst = (b1 - b0 + kSdBlocks - 1) / kSdBlocks;
+    const int row0 = a.win_row0[w];
+    const uint32_t stage_bytes = (uint32_t)(kSdBlocks * KB * 1024);
+    if (tid == 0) {
+        mbar_init(full, 1);
+        mbar_init(xfull, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&mdone[i], 1);
+            mbar_init(&epi_done[i], kTcThreads);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(tslot, 32);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t taddr = *tslot;
+
+    float xs[kBR];  // E4M3: the window rows' X scales
+#pragma unroll
+    for (int r = 0; r < kBR; ++r) xs[r] = FP8 && row0 + r < a.M ? __ldg(a.x_scale + row0 + r) : 1.0f;
+    constexpr unsigned kMask = (1u << kIssuers) - 1u;
+    // stage ch's copies: one TMA box per block (its 8 Y rows, all K-blocks); blocks past the
+    // window's end and padding blocks read rows past Y's end, which arrive as zeros
+    auto issue_stage = [&](int ch) {
+        if (lane == 0) mbar_expect_tx(full, stage_bytes);
+        __syncwarp(kMask);
+        for (int q = lane; q < kSdBlocks; q += kIssuers) {
+            const int blk = b0 + ch * kSdBlocks + q;
+            const int col = blk < b1 ? a.blk_col[blk] : -1;
+            tma_load_3d(stage + q * KB * 1024, &tmY, full, 0, col >= 0 ? col * kBC : a.Ny, 0);
+        }
+    };
+    if (warp == 0 && lane < kIssuers) {
+        if (lane == 0) {
+            mbar_expect_tx(xfull, (uint32_t)(2 * KB * 1024));
+            tma_load_3d(xt, &tmX, xfull, 0, row0, 0);
+        }
+        if (nst > 0) issue_stage(0);
+    }
+    bool ok = true;
+    bool x_landed = false;
+    int unlanded = -1;  // a stage whose copies the MMA thread gave up waiting for
+    for (int ch = 0; ch < nst; ++ch) {
+        const int buf = ch & 1;
+        if (tid == 32) {
+            if (!x_landed) x_landed = mbar_wait(xfull, 0);
+            const bool landed = mbar_wait(full, ch & 1);
+            if (!landed) unlanded = ch;
+            bool go = x_landed && landed;
+            if (go && ch >= 2) go = mbar_wait(&epi_done[buf], ((ch >> 1) - 1) & 1);
+            if (!go) {
+                atomicExch(a.err, 3);
+                ok = false;
+            } else {
+                fence_after_sync();
+                const uint32_t sa = smem_u32(stage), sx = smem_u32(xt);
+                for (int kb = 0; kb < KB; ++kb) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint64_t adesc = smem_desc(sa + kb * 1024 + j * 32, 16, KB * 1024);
+                        const uint64_t bdesc = smem_desc(sx + kb * 2048 + j * 32, 16, 1024);
+                        const uint32_t acc = (kb > 0 || j > 0) ? 1u : 0u;
+                        if constexpr (FP8)
+                            mma_e4m3(taddr + buf * 16, adesc, bdesc, kIdesc, acc);
+                        else
+                            mma_bf16(taddr + buf * 16, adesc, bdesc, kIdesc, acc);
+                    }
+                }
+            }
+            mma_commit(&mdone[buf]);  // also when skipped, so the waits below end
+        }
+        __syncwarp();
+        const bool have = mbar_wait(&mdone[buf], (ch >> 1) & 1);  // this stage's MMAs are done
+        fence_after_sync();
+        if (!have && lane == 0) atomicExch(a.err, 4);
+        // the stage buffer is free again: copy the next stage while this one's results go out
+        if (warp == 0 && lane < kIssuers && ch + 1 < nst && have) issue_stage(ch + 1);
+        __syncwarp();
+        float v[16];
+        tmem_ld16(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * 16), v);
+        const int m = 32 * warp + lane;  // gathered Y row: block m / 8, column m % 8
+        const int blk = b0 + ch * kSdBlocks + (m >> 3), c = m & 7;
+        const int col = have && ok && blk < b1 ? a.blk_col[blk] : -1;
+        if (col >= 0) {
+            // the block's 16 row masks and first positions in four 16-byte loads each, then
+            // every stored entry's value, then the stores: two memory latencies per stage
+            uint4 mk4[4], st4[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                mk4[i] = __ldg(reinterpret_cast<const uint4 *>(a.bmask + (int64_t)blk * kBR) + i);
+                st4[i] = __ldg(reinterpret_cast<const uint4 *>(a.bstart + (int64_t)blk * kBR) + i);
+            }
+            const int64_t j = (int64_t)col * kBC + c;  // past Y's end in a ragged last block column
+            const float ys = FP8 && j < a.Ny ? __ldg(a.y_scale + j) : 1.0f;
+            int64_t pos[kBR];
+            float sv[kBR];
+#pragma unroll
+            for (int r = 0; r < kBR; ++r) {
+                const uint4 &mq = mk4[r >> 2], &sq = st4[r >> 2];
+                const uint32_t mk = (r & 3) == 0 ? mq.x : (r & 3) == 1 ? mq.y : (r & 3) == 2 ? mq.z : mq.w;
+                const uint32_t st = (r & 3) == 0 ? sq.x : (r & 3) == 1 ? sq.y : (r & 3) == 2 ? sq.z : sq.w;
+                pos[r] = ((mk >> c) & 1u) ? (int64_t)(int32_t)st + __popc(mk & ((1u << c) - 1u)) : -1;
+                sv[r] = pos[r] >= 0 ? __ldg(a.svals + pos[r]) : 0.f;
+            }
+#pragma unroll
+            for (int r = 0; r < kBR; ++r) {
+                if (pos[r] < 0) continue;
+                float val = sv[r] * v[r];
+                if (FP8) val *= xs[r] * ys;
+                a.out[pos[r]] = val;
+            }
+        }
+        fence_before_sync();
+        mbar_arrive(&epi_done[buf]);
+    }
+    // copies the MMA thread gave up on (after a timeout) land before the CTA leaves
+    if (tid == 32) {
+        if (unlanded >= 0) mbar_wait(full, unlanded & 1);
+        if (!x_landed) mbar_wait(xfull, 0);
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(taddr, 32);
+}
+
 }  // namespace tc
 }  // namespace gbsp
 
@@ -583,6 +764,9 @@ struct gbsp_plan {
     uint8_t *qtiles;     // E4M3: A's codes in the same tile layout
     float *wscale;       // E4M3: per window row scale of the requantised tiles
     float *res_scale;    // E4M3: A's row scales (the residual's)
+    int32_t *bstart;     // per dense block and block row: CSR position of its first entry
+    uint32_t *bmask;     // per dense block and block row: stored columns (8 bits)
+    int32_t *res_pos;    // per residual entry: its CSR position in A
     int32_t *res_rowptr, *res_colidx;
     void *res_vals;
     int *err;
@@ -615,6 +799,9 @@ void plan_free(gbsp_plan *p) {
     cudaFree(p->res_rowptr);
     cudaFree(p->res_colidx);
     cudaFree(p->res_vals);
+    cudaFree(p->bstart);
+    cudaFree(p->bmask);
+    cudaFree(p->res_pos);
     cudaFree(p->err);
     delete p;
 }
@@ -743,15 +930,18 @@ GBSP_EXPORT int gbsp_plan_create(const gbsp_csr *A, int32_t threshold, const gbs
         cudaMemsetAsync(p->qtiles, 0, (size_t)(p->nblocks / bps) * kATile, s);
         if (M > 0) cudaMemcpyAsync(p->res_scale, A->row_scale, sizeof(float) * (size_t)M, cudaMemcpyDeviceToDevice, s);
     }
+    GBSP_TRY(dev_alloc(&p->bstart, (size_t)p->nblocks * kBR));
+    GBSP_TRY(dev_alloc(&p->bmask, (size_t)p->nblocks * kBR));
+    cudaMemsetAsync(p->bmask, 0, sizeof(uint32_t) * (size_t)p->nblocks * kBR, s);
     if (M > 0) {
         fill_blocks_kernel<<<(unsigned)nwin, 256, 0, s>>>(slot, (int)nbc, win_off, win_nb, tc_index, p->blk_col,
                                                           p->tc_row0, p->tc_blk);
         if (fp8)
             fill_values_kernel<true><<<row_blocks, 256, 0, s>>>(A->rowptr, A->colidx, A->vals, (int)M, (int)nbc, slot,
-                                                                win_off, p->qtiles, res_len);
+                                                                win_off, p->qtiles, res_len, p->bstart, p->bmask);
         else
             fill_values_kernel<false><<<row_blocks, 256, 0, s>>>(A->rowptr, A->colidx, A->vals, (int)M, (int)nbc, slot,
-                                                                 win_off, p->atiles, res_len);
+                                                                 win_off, p->atiles, res_len, p->bstart, p->bmask);
         count_launches(2);
         GBSP_TRY(check_launch("plan fill"));
     }
@@ -762,6 +952,7 @@ GBSP_EXPORT int gbsp_plan_create(const gbsp_csr *A, int32_t threshold, const gbs
     p->res_nnz = totals[0];
     p->dense_nnz = p->nnz - p->res_nnz;
     GBSP_TRY(dev_alloc(&p->res_colidx, (size_t)p->res_nnz));
+    GBSP_TRY(dev_alloc(&p->res_pos, (size_t)p->res_nnz));
     if (fp8) {
         GBSP_TRY(dev_alloc(reinterpret_cast<uint8_t **>(&p->res_vals), (size_t)p->res_nnz));
     } else {
@@ -771,11 +962,11 @@ GBSP_EXPORT int gbsp_plan_create(const gbsp_csr *A, int32_t threshold, const gbs
         if (fp8)
             fill_residual_kernel<uint8_t><<<row_blocks, 256, 0, s>>>(
                 A->rowptr, A->colidx, static_cast<const uint8_t *>(A->vals), (int)M, (int)nbc, slot, p->res_rowptr,
-                p->res_colidx, static_cast<uint8_t *>(p->res_vals));
+                p->res_colidx, static_cast<uint8_t *>(p->res_vals), p->res_pos);
         else
             fill_residual_kernel<uint16_t><<<row_blocks, 256, 0, s>>>(
                 A->rowptr, A->colidx, static_cast<const uint16_t *>(A->vals), (int)M, (int)nbc, slot, p->res_rowptr,
-                p->res_colidx, static_cast<uint16_t *>(p->res_vals));
+                p->res_colidx, static_cast<uint16_t *>(p->res_vals), p->res_pos);
         count_launches(1);
         GBSP_TRY(check_launch("plan residual"));
     }
@@ -882,6 +1073,99 @@ GBSP_EXPORT int gbsp_plan_execute(const gbsp_plan *p, const gbsp_dense *B, gbsp_
     TcArgs args{p->tc_row0, p->tc_blk, p->blk_col, p->atiles, static_cast<float *>(C->data), C->ld, (int)p->M,
                 (int)p->K, (int)N, p->err, block_box, p->withhold, p->wscale};
     st = fp8 ? launch_tc_nt<true>(nt, map, args, p->nwin_tc, s) : launch_tc_nt<false>(nt, map, args, p->nwin_tc, s);
+    return st ? st : ok();
+}
+
+namespace {
+
+// 3-D atom view of a row-major matrix whose rows are `kb` whole 128-byte atoms: dims
+// (atom elements, rows, atoms), a box of `box_rows` rows and all atoms.
+int encode_atom_view(const gbsp_dense *D, bool fp8, int kb, int box_rows, CUtensorMap *map) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return fail(GBSP_ERR_CUDA, "plan sddmm: cuTensorMapEncodeTiled is not available");
+    const int es = fp8 ? 1 : 2, atom = 128 / es;
+    const cuuint64_t dims[3] = {(cuuint64_t)atom, (cuuint64_t)D->rows, (cuuint64_t)kb};
+    const cuuint64_t strides[2] = {(cuuint64_t)D->ld * es, 128};
+    const cuuint32_t box[3] = {(cuuint32_t)atom, (cuuint32_t)box_rows, (cuuint32_t)kb};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (enc(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, D->data, dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return fail(GBSP_ERR_CUDA, "plan sddmm: tensor map encoding failed");
+    return GBSP_OK;
+}
+
+template <bool FP8>
+int launch_tc_sddmm(const CUtensorMap &my, const CUtensorMap &mx, const TcSddmmArgs &args, int nwin, cudaStream_t s) {
+    constexpr int kMaxSmem = 18 * 8 * 1024 + 1024 + 128;  // KB <= 8
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return fail(GBSP_ERR_UNSUPPORTED, "tc sddmm: device ordinal %d", dev);
+    if (!attr_set[dev]) {
+        if (cudaFuncSetAttribute(tc_sddmm_kernel<FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) !=
+            cudaSuccess)
+            return check_launch("tc sddmm smem attribute");
+        attr_set[dev] = true;
+    }
+    const int smem = 18 * args.KB * 1024 + 1024 + 128;
+    tc_sddmm_kernel<FP8><<<nwin, kTcThreads, smem, s>>>(my, mx, args);
+    count_launches(1);
+    return check_launch("tc sddmm kernel");
+}
+
+}  // namespace
+
+GBSP_EXPORT int gbsp_plan_sddmm(const gbsp_plan *p, const float *svals, const gbsp_dense *X, const gbsp_dense *Y,
+                                float *out, void *stream) {
+    if (!p || !X || !Y) return fail(GBSP_ERR_INVALID_ARG, "plan sddmm: null argument");
+    if (p->nnz > 0 && (!svals || !out)) return fail(GBSP_ERR_INVALID_ARG, "plan sddmm: null svals / out");
+    if (X->dtype != Y->dtype || (X->dtype != GBSP_BF16 && X->dtype != GBSP_E4M3))
+        return fail(GBSP_ERR_UNSUPPORTED, "plan sddmm: X and Y must both be BF16 or both E4M3");
+    if (X->rows != p->M || Y->rows != p->K || X->cols != Y->cols || X->ld < X->cols || Y->ld < Y->cols)
+        return fail(GBSP_ERR_INVALID_ARG, "plan sddmm: shape mismatch");
+    const bool fp8 = X->dtype == GBSP_E4M3;
+    if (fp8 && ((X->rows > 0 && !X->row_scale) || (Y->rows > 0 && !Y->row_scale)))
+        return fail(GBSP_ERR_INVALID_ARG, "plan sddmm: E4M3 X and Y need row scales");
+    const int64_t Kd = X->cols;
+    const int es = fp8 ? 1 : 2, V = 16 / es;
+    if (Kd % V || X->ld % V || Y->ld % V || !aligned16(X->data) || !aligned16(Y->data) || Kd > 32 * 16)
+        return fail(GBSP_ERR_ALIGN, "plan sddmm: Kd and leading dimensions multiples of %d, 16-byte aligned X and "
+                                    "Y, Kd <= 512", V);
+    const int kb = (int)(Kd * es / 128);
+    if (p->nwin_tc > 0 && ((Kd * es) % 128 || kb < 1 || kb > 8))
+        return fail(GBSP_ERR_UNSUPPORTED, "plan sddmm: tensor-core tiles need Kd a multiple of %d and at most %d",
+                    128 / es, 1024 / es);
+    if (p->nnz == 0 || Kd == 0) return ok();
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int st;
+    if (p->res_nnz > 0) {  // residual entries through the row-split kernel, at their own positions
+        SddmmProblem q{};
+        q.M = (int32_t)p->M;
+        q.N = (int32_t)p->K;
+        q.Kd = (int32_t)Kd;
+        q.nnz = p->res_nnz;
+        q.rowptr = p->res_rowptr;
+        q.colidx = p->res_colidx;
+        q.svals = svals;
+        q.X = X->data;
+        q.ldx = X->ld;
+        q.x_scale = static_cast<const float *>(X->row_scale);
+        q.Y = Y->data;
+        q.ldy = Y->ld;
+        q.y_scale = static_cast<const float *>(Y->row_scale);
+        q.out = out;
+        q.dtype = X->dtype;
+        q.pos = p->res_pos;
+        if ((st = launch_sddmm(q, GBSP_VARIANT_ROWSPLIT, 0, s))) return st;
+    }
+    if (p->nwin_tc == 0) return ok();
+    CUtensorMap my, mx;
+    if ((st = encode_atom_view(Y, fp8, kb, kBC, &my)) || (st = encode_atom_view(X, fp8, kb, kBR, &mx))) return st;
+    TcSddmmArgs args{p->tc_row0, p->tc_blk, p->blk_col, p->bstart, p->bmask, svals, out,
+                     static_cast<const float *>(X->row_scale), static_cast<const float *>(Y->row_scale),
+                     (int)p->M, (int)p->K, kb, p->err};
+    st = fp8 ? launch_tc_sddmm<true>(my, mx, args, p->nwin_tc, s) : launch_tc_sddmm<false>(my, mx, args, p->nwin_tc, s);
     return st ? st : ok();
 }
 
