@@ -593,6 +593,7 @@ struct TcSddmmArgs {
     float *out;
     const float *x_scale, *y_scale;  // E4M3 per-row scales of X and Y, else null
     int M, Ny, KB;                   // rows of X and of Y; 128-byte K-blocks per row
+    int KH;                          // K-blocks per copy unit (KB a multiple of KH)
     int *err;
 };
 
@@ -602,30 +603,35 @@ __global__ void __launch_bounds__(128) tc_sddmm_kernel(const __grid_constant__ C
                                                        const TcSddmmArgs a) {
     constexpr uint32_t kIdesc = (1u << 4) | ((FP8 ? 0u : 1u) << 7) | ((FP8 ? 0u : 1u) << 10) | ((16u >> 3) << 17) |
                                 ((128u >> 4) << 24);  // FP32 D, both operands K-major, M = 128, N = 16
+    const int KH = a.KH;  // K-blocks per unit: one copy box per block covers KH 128-byte K-blocks
+    const uint32_t kUnitBytes = (uint32_t)(kSdBlocks * KH * 1024);
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int KB = a.KB;
-    uint8_t *stage = smem;                              // [16 blocks][KB][8 rows][128 B]
-    uint8_t *xt = smem + kSdBlocks * KB * 1024;         // [KB][16 rows][128 B]
-    uint64_t *full = reinterpret_cast<uint64_t *>(xt + 2 * KB * 1024);
-    uint64_t *xfull = full + 1;
-    uint64_t *mdone = full + 2;     // [2]
-    uint64_t *epi_done = full + 4;  // [2]
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(full + 6);
+    uint8_t *slots = smem;                  // [2][16 blocks][KH][8 rows][128 B]
+    uint8_t *xt = smem + 2 * kUnitBytes;    // [KB][16 rows][128 B]
+    uint64_t *full = reinterpret_cast<uint64_t *>(xt + 2 * KB * 1024);  // [2] per slot
+    uint64_t *freed = full + 2;             // [2] per slot: its unit's MMAs are done
+    uint64_t *mdone = full + 4;             // [2] per TMEM buffer: a stage's MMAs are done
+    uint64_t *epi_done = full + 6;          // [2] per TMEM buffer: its epilogue has read it
+    uint64_t *xfull = full + 8;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(full + 9);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int w = blockIdx.x;
     const int b0 = a.win_blk[w], b1 = a.win_blk[w + 1];
     const int nst = (b1 - b0 + kSdBlocks - 1) / kSdBlocks;
+    const int NU = KB / KH;       // units per stage
+    const int nunits = nst * NU;  // unit u: stage u / NU, K-blocks (u % NU) * KH ...
     const int row0 = a.win_row0[w];
-    const uint32_t stage_bytes = (uint32_t)(kSdBlocks * KB * 1024);
     if (tid == 0) {
-        mbar_init(full, 1);
-        mbar_init(xfull, 1);
         for (int i = 0; i < 2; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&freed[i], 1);
             mbar_init(&mdone[i], 1);
             mbar_init(&epi_done[i], kTcThreads);
         }
+        mbar_init(xfull, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) tmem_alloc(tslot, 32);
@@ -638,62 +644,74 @@ __global__ void __launch_bounds__(128) tc_sddmm_kernel(const __grid_constant__ C
 #pragma unroll
     for (int r = 0; r < kBR; ++r) xs[r] = FP8 && row0 + r < a.M ? __ldg(a.x_scale + row0 + r) : 1.0f;
     constexpr unsigned kMask = (1u << kIssuers) - 1u;
-    // stage ch's copies: one TMA box per block (its 8 Y rows, all K-blocks); blocks past the
-    // window's end and padding blocks read rows past Y's end, which arrive as zeros
-    auto issue_stage = [&](int ch) {
-        if (lane == 0) mbar_expect_tx(full, stage_bytes);
+    // unit u's copies into slot u % 2: one TMA box per block (8 Y rows, one K-block); blocks
+    // past the window's end and padding blocks read rows past Y's end, which arrive as zeros
+    auto issue_unit = [&](int u) {
+        const int ch = u / NU, kb = (u % NU) * KH;
+        if (lane == 0) mbar_expect_tx(&full[u & 1], kUnitBytes);
         __syncwarp(kMask);
         for (int q = lane; q < kSdBlocks; q += kIssuers) {
             const int blk = b0 + ch * kSdBlocks + q;
             const int col = blk < b1 ? a.blk_col[blk] : -1;
-            tma_load_3d(stage + q * KB * 1024, &tmY, full, 0, col >= 0 ? col * kBC : a.Ny, 0);
+            tma_load_3d(slots + (u & 1) * kUnitBytes + q * KH * 1024, &tmY, &full[u & 1], 0,
+                        col >= 0 ? col * kBC : a.Ny, kb);
         }
     };
-    if (warp == 0 && lane < kIssuers) {
+    const bool producer = warp == 0 && lane < kIssuers;
+    if (producer) {
         if (lane == 0) {
             mbar_expect_tx(xfull, (uint32_t)(2 * KB * 1024));
             tma_load_3d(xt, &tmX, xfull, 0, row0, 0);
         }
-        if (nst > 0) issue_stage(0);
+        for (int u = 0; u < 2 && u < nunits; ++u) issue_unit(u);
     }
     bool ok = true;
     bool x_landed = false;
-    int unlanded = -1;  // a stage whose copies the MMA thread gave up waiting for
+    int unlanded = -1;  // a unit whose copies the MMA thread gave up waiting for
     for (int ch = 0; ch < nst; ++ch) {
         const int buf = ch & 1;
-        if (tid == 32) {
-            if (!x_landed) x_landed = mbar_wait(xfull, 0);
-            const bool landed = mbar_wait(full, ch & 1);
-            if (!landed) unlanded = ch;
-            bool go = x_landed && landed;
-            if (go && ch >= 2) go = mbar_wait(&epi_done[buf], ((ch >> 1) - 1) & 1);
-            if (!go) {
-                atomicExch(a.err, 3);
-                ok = false;
-            } else {
-                fence_after_sync();
-                const uint32_t sa = smem_u32(stage), sx = smem_u32(xt);
-                for (int kb = 0; kb < KB; ++kb) {
+        for (int h = 0; h < NU; ++h) {
+            const int u = ch * NU + h;
+            if (tid == 32) {
+                if (!x_landed) x_landed = mbar_wait(xfull, 0);
+                const bool landed = mbar_wait(&full[u & 1], (u >> 1) & 1);
+                if (!landed) unlanded = u;
+                bool go = x_landed && landed && ok;
+                if (go && h == 0 && ch >= 2) go = mbar_wait(&epi_done[buf], ((ch >> 1) - 1) & 1);
+                if (!go) {
+                    if (ok) atomicExch(a.err, 3);
+                    ok = false;
+                } else {
+                    fence_after_sync();
+                    const uint32_t sa = smem_u32(slots + (u & 1) * kUnitBytes), sx = smem_u32(xt);
+                    for (int kk = 0; kk < KH; ++kk) {
+                        const int kb = h * KH + kk;
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const uint64_t adesc = smem_desc(sa + kb * 1024 + j * 32, 16, KB * 1024);
-                        const uint64_t bdesc = smem_desc(sx + kb * 2048 + j * 32, 16, 1024);
-                        const uint32_t acc = (kb > 0 || j > 0) ? 1u : 0u;
-                        if constexpr (FP8)
-                            mma_e4m3(taddr + buf * 16, adesc, bdesc, kIdesc, acc);
-                        else
-                            mma_bf16(taddr + buf * 16, adesc, bdesc, kIdesc, acc);
+                        for (int j = 0; j < 4; ++j) {
+                            const uint64_t adesc = smem_desc(sa + kk * 1024 + j * 32, 16, KH * 1024);
+                            const uint64_t bdesc = smem_desc(sx + kb * 2048 + j * 32, 16, 1024);
+                            const uint32_t acc = (kb > 0 || j > 0) ? 1u : 0u;
+                            if constexpr (FP8)
+                                mma_e4m3(taddr + buf * 16, adesc, bdesc, kIdesc, acc);
+                            else
+                                mma_bf16(taddr + buf * 16, adesc, bdesc, kIdesc, acc);
+                        }
                     }
                 }
+                mma_commit(&freed[u & 1]);  // also when skipped, so the waits end
+                if (h == NU - 1) mma_commit(&mdone[buf]);
             }
-            mma_commit(&mdone[buf]);  // also when skipped, so the waits below end
+            // the slot of unit u is refilled with unit u + 2 once unit u's MMAs are done
+            if (producer && u + 2 < nunits) {
+                const bool got = mbar_wait(&freed[u & 1], (u >> 1) & 1);
+                if (__all_sync(kMask, got)) issue_unit(u + 2);
+                else if (lane == 0) atomicExch(a.err, 5);
+            }
         }
         __syncwarp();
         const bool have = mbar_wait(&mdone[buf], (ch >> 1) & 1);  // this stage's MMAs are done
         fence_after_sync();
         if (!have && lane == 0) atomicExch(a.err, 4);
-        // the stage buffer is free again: copy the next stage while this one's results go out
-        if (warp == 0 && lane < kIssuers && ch + 1 < nst && have) issue_stage(ch + 1);
         __syncwarp();
         float v[16];
         tmem_ld16(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * 16), v);
@@ -734,7 +752,7 @@ __global__ void __launch_bounds__(128) tc_sddmm_kernel(const __grid_constant__ C
     }
     // copies the MMA thread gave up on (after a timeout) land before the CTA leaves
     if (tid == 32) {
-        if (unlanded >= 0) mbar_wait(full, unlanded & 1);
+        if (unlanded >= 0) mbar_wait(&full[unlanded & 1], (unlanded >> 1) & 1);
         if (!x_landed) mbar_wait(xfull, 0);
     }
     fence_before_sync();
@@ -1079,14 +1097,14 @@ GBSP_EXPORT int gbsp_plan_execute(const gbsp_plan *p, const gbsp_dense *B, gbsp_
 namespace {
 
 // 3-D atom view of a row-major matrix whose rows are `kb` whole 128-byte atoms: dims
-// (atom elements, rows, atoms), a box of `box_rows` rows and all atoms.
-int encode_atom_view(const gbsp_dense *D, bool fp8, int kb, int box_rows, CUtensorMap *map) {
+// (atom elements, rows, atoms), a box of `box_rows` rows and `box_atoms` atoms.
+int encode_atom_view(const gbsp_dense *D, bool fp8, int kb, int box_rows, int box_atoms, CUtensorMap *map) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return fail(GBSP_ERR_CUDA, "plan sddmm: cuTensorMapEncodeTiled is not available");
     const int es = fp8 ? 1 : 2, atom = 128 / es;
     const cuuint64_t dims[3] = {(cuuint64_t)atom, (cuuint64_t)D->rows, (cuuint64_t)kb};
     const cuuint64_t strides[2] = {(cuuint64_t)D->ld * es, 128};
-    const cuuint32_t box[3] = {(cuuint32_t)atom, (cuuint32_t)box_rows, (cuuint32_t)kb};
+    const cuuint32_t box[3] = {(cuuint32_t)atom, (cuuint32_t)box_rows, (cuuint32_t)box_atoms};
     const cuuint32_t estr[3] = {1, 1, 1};
     if (enc(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, D->data, dims, strides, box,
             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -1097,7 +1115,7 @@ int encode_atom_view(const gbsp_dense *D, bool fp8, int kb, int box_rows, CUtens
 
 template <bool FP8>
 int launch_tc_sddmm(const CUtensorMap &my, const CUtensorMap &mx, const TcSddmmArgs &args, int nwin, cudaStream_t s) {
-    constexpr int kMaxSmem = 18 * 8 * 1024 + 1024 + 128;  // KB <= 8
+    constexpr int kMaxSmem = 2 * 2 * 16 * 1024 + 2 * 8 * 1024 + 1024 + 128;  // KH <= 2, KB <= 8
     static bool attr_set[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1108,7 +1126,7 @@ int launch_tc_sddmm(const CUtensorMap &my, const CUtensorMap &mx, const TcSddmmA
             return check_launch("tc sddmm smem attribute");
         attr_set[dev] = true;
     }
-    const int smem = 18 * args.KB * 1024 + 1024 + 128;
+    const int smem = 2 * args.KH * 16 * 1024 + 2 * args.KB * 1024 + 1024 + 128;  // two unit slots, X rows, barriers
     tc_sddmm_kernel<FP8><<<nwin, kTcThreads, smem, s>>>(my, mx, args);
     count_launches(1);
     return check_launch("tc sddmm kernel");
@@ -1161,10 +1179,14 @@ GBSP_EXPORT int gbsp_plan_sddmm(const gbsp_plan *p, const float *svals, const gb
     }
     if (p->nwin_tc == 0) return ok();
     CUtensorMap my, mx;
-    if ((st = encode_atom_view(Y, fp8, kb, kBC, &my)) || (st = encode_atom_view(X, fp8, kb, kBR, &mx))) return st;
+    // copy units of one K-block (16 KB): two unit slots leave room for 5-6 CTAs per SM (two
+    // K-blocks per unit, 3 CTAs per SM, measured 1.6x slower for E4M3 at Kd = 256)
+    const int kh = 1;
+    if ((st = encode_atom_view(Y, fp8, kb, kBC, kh, &my)) || (st = encode_atom_view(X, fp8, kb, kBR, kb, &mx)))
+        return st;
     TcSddmmArgs args{p->tc_row0, p->tc_blk, p->blk_col, p->bstart, p->bmask, svals, out,
                      static_cast<const float *>(X->row_scale), static_cast<const float *>(Y->row_scale),
-                     (int)p->M, (int)p->K, kb, p->err};
+                     (int)p->M, (int)p->K, kb, kh, p->err};
     st = fp8 ? launch_tc_sddmm<true>(my, mx, args, p->nwin_tc, s) : launch_tc_sddmm<false>(my, mx, args, p->nwin_tc, s);
     return st ? st : ok();
 }
