@@ -26,7 +26,10 @@ int run(const SddmmProblem &P, int variant, cudaStream_t s) {
         count_launches(1);
         return check_launch("sddmm merge");
     }
-    sddmm_rowsplit_kernel<EL, LPN, VPL><<<dim3((P.M + 7) / 8), 256, 0, s>>>(P);
+    if (P.pos)  // a plan's residual: values and outputs at the entries' original positions
+        sddmm_rowsplit_kernel<EL, LPN, VPL, true><<<dim3((P.M + 7) / 8), 256, 0, s>>>(P);
+    else
+        sddmm_rowsplit_kernel<EL, LPN, VPL><<<dim3((P.M + 7) / 8), 256, 0, s>>>(P);
     count_launches(1);
     return check_launch("sddmm rowsplit");
 }

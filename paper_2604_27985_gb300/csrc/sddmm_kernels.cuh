@@ -52,10 +52,10 @@ __device__ __forceinline__ void sddmm_chunk(const uint4 *__restrict__ Yv, int64_
 }
 
 // Entries [p0, p1) of row `row`: X_i in registers, entries 32 at a time with the next 32
-// column indices and values prefetched while the current ones are used.  With P.pos, entry
+// column indices and values prefetched while the current ones are used.  With POS, entry
 // e's value and output sit at position P.pos[e] of the caller's arrays (a sub-matrix of
 // another CSR, such as the residual of a tensor-core plan).
-template <class EL, int LPN, int VPL, bool CHECK_COLS>
+template <class EL, int LPN, int VPL, bool CHECK_COLS, bool POS = false>
 __device__ __forceinline__ void sddmm_segment(const SddmmProblem &P, int row, int64_t p0, int64_t p1, int lane) {
     const int sl = lane % LPN, g = lane / LPN;
     using ST = typename EL::stored;
@@ -80,7 +80,7 @@ __device__ __forceinline__ void sddmm_segment(const SddmmProblem &P, int row, in
     int64_t q = p0 + lane;  // where this lane's entry keeps its value and output
     if (p0 + lane < p1) {
         c = ld_stream(P.colidx + p0 + lane);
-        if (P.pos) q = __ldg(P.pos + p0 + lane);
+        if constexpr (POS) q = __ldg(P.pos + p0 + lane);
         s = ld_stream(P.svals + q);
     }
     for (int64_t base = p0; base < p1; base += 32) {
@@ -90,7 +90,7 @@ __device__ __forceinline__ void sddmm_segment(const SddmmProblem &P, int row, in
         int64_t q2 = nb + lane;
         if (nb + lane < p1) {
             c2 = ld_stream(P.colidx + nb + lane);
-            if (P.pos) q2 = __ldg(P.pos + nb + lane);
+            if constexpr (POS) q2 = __ldg(P.pos + nb + lane);
             s2 = ld_stream(P.svals + q2);
         }
         float part[LPN];
@@ -111,25 +111,25 @@ __device__ __forceinline__ void sddmm_segment(const SddmmProblem &P, int row, in
         if (base + lane < p1) {
             float r = s * part[0];
             if (EL::dtype == GBSP_E4M3) r *= xs * __ldg(P.y_scale + c);
-            __stcs(P.out + q, r);
+            __stcs(P.out + (POS ? q : base + lane), r);
         }
         c = c2;
-        q = q2;
+        if constexpr (POS) q = q2;
         s = s2;
     }
 }
 
 // One warp per row of S.
-template <class EL, int LPN, int VPL>
+template <class EL, int LPN, int VPL, bool POS = false>
 __global__ void __launch_bounds__(256) sddmm_rowsplit_kernel(const SddmmProblem P) {
     const int lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= P.M) return;
     const int64_t p0 = __ldg(P.rowptr + row), p1 = __ldg(P.rowptr + row + 1);
     if (P.Kd == LPN * VPL * EL::V)
-        sddmm_segment<EL, LPN, VPL, false>(P, row, p0, p1, lane);
+        sddmm_segment<EL, LPN, VPL, false, POS>(P, row, p0, p1, lane);
     else
-        sddmm_segment<EL, LPN, VPL, true>(P, row, p0, p1, lane);
+        sddmm_segment<EL, LPN, VPL, true, POS>(P, row, p0, p1, lane);
 }
 
 // nnz-balanced split: warp w takes the items [w * ipw, (w + 1) * ipw) of the merge path
