@@ -199,10 +199,14 @@ int gbsp_plan_execute(const gbsp_plan *plan, const gbsp_dense *B, gbsp_dense *C,
  * memory (TMA), FP32 accumulation in tensor memory, and the epilogue writes the stored
  * entries only.  Requirements: Kd and both leading dimensions multiples of 16 bytes' worth
  * of elements, 16-byte aligned X and Y, Kd <= 512 (GBSP_ERR_ALIGN otherwise); when any
- * window is dense, Kd a multiple of 64 (BF16) or 128 (E4M3) (GBSP_ERR_UNSUPPORTED).
- * Asynchronous; waits are bounded as in gbsp_plan_execute (see gbsp_plan_check). */
+ * window is dense and the tiles are used, Kd a multiple of 64 (BF16) or 128 (E4M3)
+ * (GBSP_ERR_UNSUPPORTED).  tiles: 1 uses the tiles as above, 0 runs every entry through the
+ * CSR kernels on the plan's copy of the pattern, < 0 chooses: the tiles when the dense
+ * blocks average at least 24 stored entries (below that, gathering a block's 8 Y rows costs
+ * more than its entries' rows).  Asynchronous; waits are bounded as in gbsp_plan_execute
+ * (see gbsp_plan_check). */
 int gbsp_plan_sddmm(const gbsp_plan *plan, const float *svals, const gbsp_dense *X, const gbsp_dense *Y, float *out,
-                    void *stream);
+                    int32_t tiles, void *stream);
 int gbsp_plan_info(const gbsp_plan *plan, int64_t *info, int n);
 int gbsp_plan_check(const gbsp_plan *plan, void *stream);
 /* Testing the timeout path (no counterpart in the paper): while chunk >= 0, the first

@@ -59,7 +59,7 @@ def _load() -> ctypes.CDLL:
         "sddmm_csr": [P, P, P, P, P, P, I64, I64, I64],
         "spmm_csr_noalloc": [P, P, P, P, P, I64, I64, I64, P],
         "gbsp_gather_probe": [P, I64, I64, I64, P, I64, P, I, I, P],
-        "gbsp_plan_sddmm": [P, P, ctypes.POINTER(Dense), ctypes.POINTER(Dense), P, P],
+        "gbsp_plan_sddmm": [P, P, ctypes.POINTER(Dense), ctypes.POINTER(Dense), P, I, P],
         "spmm_csr_ex": [ctypes.POINTER(Csr), ctypes.POINTER(Dense), ctypes.POINTER(Dense), ctypes.POINTER(Opts), P],
         "sddmm_csr_ex": [ctypes.POINTER(Csr), ctypes.POINTER(Dense), ctypes.POINTER(Dense), P,
                          ctypes.POINTER(Opts), P],

@@ -785,6 +785,7 @@ struct gbsp_plan {
     int32_t *bstart;     // per dense block and block row: CSR position of its first entry
     uint32_t *bmask;     // per dense block and block row: stored columns (8 bits)
     int32_t *res_pos;    // per residual entry: its CSR position in A
+    int32_t *rowptr_full, *colidx_full;  // A's pattern, for an SDDMM that skips the tiles
     int32_t *res_rowptr, *res_colidx;
     void *res_vals;
     int *err;
@@ -820,6 +821,8 @@ void plan_free(gbsp_plan *p) {
     cudaFree(p->bstart);
     cudaFree(p->bmask);
     cudaFree(p->res_pos);
+    cudaFree(p->rowptr_full);
+    cudaFree(p->colidx_full);
     cudaFree(p->err);
     delete p;
 }
@@ -971,6 +974,11 @@ GBSP_EXPORT int gbsp_plan_create(const gbsp_csr *A, int32_t threshold, const gbs
     p->dense_nnz = p->nnz - p->res_nnz;
     GBSP_TRY(dev_alloc(&p->res_colidx, (size_t)p->res_nnz));
     GBSP_TRY(dev_alloc(&p->res_pos, (size_t)p->res_nnz));
+    GBSP_TRY(dev_alloc(&p->rowptr_full, (size_t)M + 1));
+    GBSP_TRY(dev_alloc(&p->colidx_full, (size_t)p->nnz));
+    if (M > 0) cudaMemcpyAsync(p->rowptr_full, A->rowptr, sizeof(int32_t) * (size_t)(M + 1), cudaMemcpyDeviceToDevice, s);
+    if (p->nnz > 0)
+        cudaMemcpyAsync(p->colidx_full, A->colidx, sizeof(int32_t) * (size_t)p->nnz, cudaMemcpyDeviceToDevice, s);
     if (fp8) {
         GBSP_TRY(dev_alloc(reinterpret_cast<uint8_t **>(&p->res_vals), (size_t)p->res_nnz));
     } else {
@@ -1135,7 +1143,7 @@ int launch_tc_sddmm(const CUtensorMap &my, const CUtensorMap &mx, const TcSddmmA
 }  // namespace
 
 GBSP_EXPORT int gbsp_plan_sddmm(const gbsp_plan *p, const float *svals, const gbsp_dense *X, const gbsp_dense *Y,
-                                float *out, void *stream) {
+                                float *out, int32_t tiles, void *stream) {
     if (!p || !X || !Y) return fail(GBSP_ERR_INVALID_ARG, "plan sddmm: null argument");
     if (p->nnz > 0 && (!svals || !out)) return fail(GBSP_ERR_INVALID_ARG, "plan sddmm: null svals / out");
     if (X->dtype != Y->dtype || (X->dtype != GBSP_BF16 && X->dtype != GBSP_E4M3))
@@ -1151,12 +1159,35 @@ GBSP_EXPORT int gbsp_plan_sddmm(const gbsp_plan *p, const float *svals, const gb
         return fail(GBSP_ERR_ALIGN, "plan sddmm: Kd and leading dimensions multiples of %d, 16-byte aligned X and "
                                     "Y, Kd <= 512", V);
     const int kb = (int)(Kd * es / 128);
-    if (p->nwin_tc > 0 && ((Kd * es) % 128 || kb < 1 || kb > 8))
+    // the tiles pay when a dense block holds enough stored entries to outweigh gathering all
+    // its 8 Y rows (measured crossover between 16 and 27 per block on 16,384^2 at 90%, Kd = 256)
+    if (tiles < 0) tiles = p->nwin_tc > 0 && p->dense_nnz >= 24 * p->nblocks;
+    if (tiles && p->nwin_tc > 0 && ((Kd * es) % 128 || kb < 1 || kb > 8))
         return fail(GBSP_ERR_UNSUPPORTED, "plan sddmm: tensor-core tiles need Kd a multiple of %d and at most %d",
                     128 / es, 1024 / es);
     if (p->nnz == 0 || Kd == 0) return ok();
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int st;
+    if (!tiles) {  // every entry through the CSR kernels on the plan's copy of the pattern
+        SddmmProblem q{};
+        q.M = (int32_t)p->M;
+        q.N = (int32_t)p->K;
+        q.Kd = (int32_t)Kd;
+        q.nnz = p->nnz;
+        q.rowptr = p->rowptr_full;
+        q.colidx = p->colidx_full;
+        q.svals = svals;
+        q.X = X->data;
+        q.ldx = X->ld;
+        q.x_scale = static_cast<const float *>(X->row_scale);
+        q.Y = Y->data;
+        q.ldy = Y->ld;
+        q.y_scale = static_cast<const float *>(Y->row_scale);
+        q.out = out;
+        q.dtype = X->dtype;
+        const int variant = p->nnz < 32 * p->M ? GBSP_VARIANT_ENTRY : GBSP_VARIANT_ROWSPLIT;
+        return (st = launch_sddmm(q, variant, 0, s)) ? st : ok();
+    }
     if (p->res_nnz > 0) {  // residual entries through the row-split kernel, at their own positions
         SddmmProblem q{};
         q.M = (int32_t)p->M;

@@ -173,13 +173,14 @@ class TcPlan:
         check(lib.gbsp_plan_execute(self._h, ctypes.byref(b), ctypes.byref(c), _stream(stream)))
         return out
 
-    def sddmm(self, svals, X, Y, out=None, x_scale=None, y_scale=None, stream=None) -> torch.Tensor:
+    def sddmm(self, svals, X, Y, out=None, x_scale=None, y_scale=None, tiles=-1, stream=None) -> torch.Tensor:
         """out[p] = svals[p] <X_i, Y_j> on the plan's pattern (gbsp_plan_sddmm): the dense
-        blocks on tcgen05, the rest on the CSR kernel; returns FP32 out[nnz]."""
+        blocks on tcgen05 and the rest on the CSR kernel (tiles=1), every entry on the CSR
+        kernels (tiles=0), or the plan's choice (tiles=-1); returns FP32 out[nnz]."""
         if out is None:
             out = torch.empty(svals.numel(), dtype=torch.float32, device=X.device)
         x, y = _dense(X, x_scale), _dense(Y, y_scale)
-        check(lib.gbsp_plan_sddmm(self._h, _ptr(svals), ctypes.byref(x), ctypes.byref(y), _ptr(out),
+        check(lib.gbsp_plan_sddmm(self._h, _ptr(svals), ctypes.byref(x), ctypes.byref(y), _ptr(out), int(tiles),
                                   _stream(stream)))
         return out
 
