@@ -532,14 +532,20 @@ __global__ void __launch_bounds__(256) fold_e4m3_kernel(const uint8_t *__restric
     const int kb = ((((t & 15) >> 1) ^ rowin) * 16 + 8 * (t & 1)) >> 3;  // block of the tile
     const int row = tc_row0[w] + r;
     const float s = row < M ? __ldg(a_scale + row) : 0.f;
+    // two codes decoded per conversion and two products per packed FP32 multiply (the same
+    // single roundings as scalar code)
     auto values = [&](int tile, float (&v)[8]) {
         const uint2 q = __ldg(reinterpret_cast<const uint2 *>(qtiles + (int64_t)(b0 / 16 + tile) * kATile) + t);
         float tk[8];
         fold_load_t(b_scale, __ldg(blk_col + b0 + tile * 16 + kb), K, vec_ok != 0, tk);
+        const float2 s2 = make_float2(s, s);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const uint8_t code = (uint8_t)(((c < 4 ? q.x : q.y) >> (8 * (c & 3))) & 0xffu);
-            v[c] = __fmul_rn(__fmul_rn(s, E4M3::value(code)), tk[c]);
+        for (int h = 0; h < 4; ++h) {
+            const uint32_t word = h < 2 ? q.x : q.y;
+            const float2 d = E4M3::pair((uint16_t)(word >> (16 * (h & 1))));
+            const float2 r = __fmul2_rn(__fmul2_rn(s2, d), make_float2(tk[2 * h], tk[2 * h + 1]));
+            v[2 * h] = r.x;
+            v[2 * h + 1] = r.y;
         }
     };
     float amax = 0.f;
@@ -564,10 +570,12 @@ __global__ void __launch_bounds__(256) fold_e4m3_kernel(const uint8_t *__restric
         float v[8];
         values(tile, v);
         uint32_t out[2] = {0u, 0u};
+        const float2 inv2 = make_float2(inv, inv);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const uint32_t code = __nv_cvt_float_to_fp8(__fmul_rn(v[c], inv), __NV_SATFINITE, __NV_E4M3);
-            out[c >> 2] |= (code & 0xffu) << (8 * (c & 3));
+        for (int h = 0; h < 4; ++h) {
+            const float2 x = __fmul2_rn(make_float2(v[2 * h], v[2 * h + 1]), inv2);
+            const uint32_t two = __nv_cvt_float2_to_fp8x2(x, __NV_SATFINITE, __NV_E4M3);  // x.x in the low byte
+            out[h >> 1] |= (two & 0xffffu) << (16 * (h & 1));
         }
         reinterpret_cast<uint2 *>(atiles + (int64_t)(b0 / 16 + tile) * kATile)[t] = make_uint2(out[0], out[1]);
     }
