@@ -588,8 +588,10 @@ __global__ void __launch_bounds__(256) fold_e4m3_kernel(const uint8_t *__restric
 // with Y_g the Y rows of 16 blocks' columns (8 each) and X_w the window's 16 X rows, both
 // K-major (Kd contiguous) in 128-byte-swizzled shared memory; the epilogue writes
 // out[p] = s_p D[j][i] only for the stored entries (Eq. 2), found from the plan's per block
-// row first position and column mask.  One stage of 16 blocks at a time; two TMEM buffers
-// let stage ch's epilogue overlap stage ch + 1's copies and MMAs.
+// row first position and column mask.  One stage of 16 blocks at a time, its Y rows
+// arriving in units of KH 128-byte K-blocks through two shared-memory slots (a slot is
+// refilled once its unit's MMAs are done); two TMEM buffers let stage ch's epilogue overlap
+// stage ch + 1's copies and MMAs.
 
 constexpr int kSdBlocks = 16;  // dense blocks per stage: MMA M = 128 gathered Y rows
 
