@@ -93,7 +93,7 @@ typedef struct {
     int32_t vecs;      /* 0 = default; else 16-byte vectors each lane moves per row (1, 2 or 4) */
 } gbsp_opts;
 
-/* ---- plain FP32 forms (spec signatures), legacy default stream --------------- */
+/* ---- plain FP32 forms (pointer-and-size signatures), legacy default stream ------------ */
 
 /* SpMM, Eq. 1: C[i, :] = sum over p in row i of vals[p] * B[colidx[p], :].
  * rowptr int32[M+1], colidx int32[nnz], vals float[nnz], B float[K x N] (ld = N),

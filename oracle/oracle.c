@@ -31,7 +31,7 @@ static int pick_threads(int nthreads) {
 int oracle_max_threads(void) { return pick_threads(0); }
 
 /*
- * SpMM, Eq. 1 (Section II-A: Y = A X with A sparse) in the spec naming C = A B:
+ * SpMM, Eq. 1 (Section II-A: Y = A X with A sparse) in this library's naming C = A B:
  *   C[i, n] = sum over p in [rowptr[i], rowptr[i+1]) of vals[p] * B[colidx[p], n]
  * which is the per-nonzero multiply-accumulate of the worker task (Section III-A-1).
  * scale[i, n] = sum of |vals[p]| * |B[colidx[p], n]| (the per-output error scale).
@@ -64,7 +64,7 @@ void oracle_spmm_f64(int64_t M, int64_t K, int64_t N, const int32_t *rowptr,
 
 /*
  * SDDMM, Eq. 2 (Section II-A: Y = A o (B C), computed only where A is nonzero,
- * Section III-B) in the spec naming, with Y here the N x Kd row-major transpose of
+ * Section III-B) in this library's naming, with Y here the N x Kd row-major transpose of
  * the paper's C:
  *   out[p] = svals[p] * sum over k of X[i, k] * Y[colidx[p], k]   for p in row i
  * scale[p] = |svals[p]| * sum over k of |X[i, k]| * |Y[colidx[p], k]|.

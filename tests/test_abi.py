@@ -30,7 +30,7 @@ def declared_functions():
     return sorted(names)
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_plain_and_descriptor_calls():
     names = declared_functions()
     for n in ("spmm_csr", "sddmm_csr", "spmm_csr_ex", "sddmm_csr_ex", "gbsp_csr_validate"):
         assert n in names
