@@ -145,6 +145,32 @@ def e4m3_rows_dequant(q, s, rowptr=None) -> np.ndarray:
     return v * np.repeat(np.asarray(s, dtype=np.float64), lengths)
 
 
+def row_softmax(rowptr, E):
+    """Softmax over each row's stored entries: a_ij = exp(E_ij - m_i) / sum_j exp(E_ij - m_i)
+    with m_i the row's largest E (the attention normalisation of a GAT layer, which the
+    paper names as the SDDMM -> SpMM use case).  Empty rows have no entries."""
+    rp = np.asarray(rowptr, dtype=np.int64)
+    E = np.asarray(E, dtype=np.float64)
+    out = np.empty_like(E)
+    for i in range(rp.size - 1):
+        a, b = rp[i], rp[i + 1]
+        if a == b:
+            continue
+        w = np.exp(E[a:b] - E[a:b].max())
+        out[a:b] = w / w.sum()
+    return out
+
+
+def gat_chain(rowptr, colidx, svals, H, threads: int = 0):
+    """Per graph: E = S o (H H^T) on the pattern of S (Eq. 2 with X = Y = H), alpha = the
+    softmax of each row's E, then O = alpha H (Eq. 1 with A's values replaced by alpha).
+    Returns alpha, O and O's scale (sum_j alpha_ij |H_jn|)."""
+    E, _ = sddmm(rowptr, colidx, svals, H, H, threads)
+    alpha = row_softmax(rowptr, E)
+    O, sO = spmm(rowptr, colidx, alpha, H, threads)
+    return alpha, O, sO
+
+
 def gnn_chain(rowptr, colidx, svals, H, threads: int = 0):
     """Per graph: E = S o (H H^T) on the pattern of S (Eq. 2 with X = Y = H), then
     O = E H (Eq. 1 with A's values replaced by E).  Returns E, O and both scales."""

@@ -281,3 +281,57 @@ def test_e4m3_rows_scale_and_max():
     qd, sd = oracle.e4m3_rows(X)
     assert qd.shape == X.shape and sd.shape == (30,)
     np.testing.assert_array_equal(sd, (np.abs(X).max(axis=1) / np.float32(448)).astype(np.float32))
+
+
+# ---- GAT-style chain: row softmax between SDDMM and SpMM --------------------------------------
+
+def test_row_softmax_hand_example():
+    """exp of [0, ln 2, ln 5] is [1, 2, 5]: weights 1/8, 2/8, 5/8; an empty row; equal scores
+    split evenly; huge scores do not overflow (the row maximum is subtracted first)."""
+    rp = np.array([0, 3, 3, 5, 7])
+    E = np.array([0.0, np.log(2.0), np.log(5.0), 10.0, 10.0, 1000.0, 999.0])
+    a = oracle.row_softmax(rp, E)
+    assert np.allclose(a[:3], [1 / 8, 2 / 8, 5 / 8], rtol=0, atol=1e-15)
+    assert np.allclose(a[3:5], [0.5, 0.5], rtol=0, atol=1e-15)
+    e = np.exp(-1.0)
+    assert np.allclose(a[5:7], [1 / (1 + e), e / (1 + e)], rtol=0, atol=1e-15)
+
+
+def test_gat_chain_against_dense_brute_force():
+    """alpha and O from the chain equal a dense masked softmax (entries outside the pattern at
+    -inf) followed by a dense product, written out with plain loops."""
+    rng = np.random.default_rng(5)
+    n, N = 9, 4
+    lengths = rng.integers(0, 5, n)
+    A = gen.csr_from_lengths(lengths, n, seed=6)
+    H = rng.normal(size=(n, N))
+    alpha, O, _ = oracle.gat_chain(A.rowptr, A.colidx, A.vals, H)
+    for i in range(n):
+        a, b = A.rowptr[i], A.rowptr[i + 1]
+        scores = np.full(n, -np.inf)
+        for p in range(a, b):
+            scores[A.colidx[p]] = A.vals[p] * sum(H[i, k] * H[A.colidx[p], k] for k in range(N))
+        if a == b:
+            assert np.all(O[i] == 0)
+            continue
+        w = np.exp(scores - scores.max())
+        w = w / w.sum()
+        for p in range(a, b):
+            assert abs(alpha[p] - w[A.colidx[p]]) <= 1e-14
+        for k in range(N):
+            assert abs(O[i, k] - sum(w[j] * H[j, k] for j in range(n))) <= 1e-12
+
+
+def test_gat_chain_invariants():
+    """Rows of alpha sum to 1 and are positive; with every H row equal to v, O_i = v on
+    non-empty rows (a convex combination of equal vectors)."""
+    A = gen.gnn_graph(300, 21)
+    H = gen.dense_normal(A.M, 16, 22).astype(np.float64)
+    alpha, _, _ = oracle.gat_chain(A.rowptr, A.colidx, A.vals, H)
+    sums = np.add.reduceat(alpha, A.rowptr[:-1][A.row_lengths() > 0])
+    assert np.allclose(sums, 1.0, rtol=0, atol=1e-12) and np.all(alpha > 0)
+    v = np.linspace(-1, 1, 16)
+    Hc = np.tile(v, (A.M, 1))
+    _, O, _ = oracle.gat_chain(A.rowptr, A.colidx, A.vals, Hc)
+    nz = A.row_lengths() > 0
+    assert np.allclose(O[nz], v, rtol=0, atol=1e-12) and np.all(O[~nz] == 0)
