@@ -502,7 +502,9 @@ def run_precision(args):
 
 def run_gnn(args):
     """512 graphs (1,000..50,000 nodes, power-law degrees with mean 16), BF16 features of
-    width 64/128/256: SDDMM -> SpMM per graph in one persistent launch from a CUDA graph."""
+    width 64/128/256: SDDMM -> SpMM per graph in one persistent launch from a CUDA graph.
+    With --gat each row's scores pass through a softmax between the two products (E then
+    holds the weights); the algorithmic bytes are the same, E being written once."""
     import torch
 
     import paper_2604_27985_gb300 as gb
@@ -517,17 +519,18 @@ def run_gnn(args):
                      torch.empty(A.nnz, dtype=torch.float32, device=dev)))
         flop += 4.0 * A.nnz * N
         gbytes += (A.nnz * (4 + 4 + 4 + 2 * N) + A.M * (4 + 2 * N + 2 * N)) / 1e9
-    plan = gb.GnnPlan(devs)
+    plan = gb.GnnPlan(devs, softmax=args.gat)
     stream = torch.cuda.current_stream()
     launches0 = gb.launch_count()
     ms = _event_ms(plan.execute, args.steps, args.warmup, stream)
     launches = (gb.launch_count() - launches0) // (args.steps + args.warmup)
     peak, _ = peaks()
     info = plan.info()
-    _line("batched SDDMM->SpMM GFLOP/s (4*nnz*N over the batch)", flop / ms / 1e6, "GFLOP/s", ms, args, "bf16",
+    chain = "SDDMM->row softmax->SpMM" if args.gat else "SDDMM->SpMM"
+    _line(f"batched {chain} GFLOP/s (4*nnz*N over the batch)", flop / ms / 1e6, "GFLOP/s", ms, args, "bf16",
           {"workload": f"{len(graphs)} of the 512 graphs (nodes log-uniform [1000, 50000], power-law degree "
                        "(mean 16, max 2048), row-normalised values, BF16 features N in {64,128,256}, seed 3000)",
-           **info},
+           "softmax": bool(args.gat), **info},
           roofline={"bound": "hbm", "kernel": "gnn_kernel, gather model", "achieved": round(gbytes / ms * 1e3, 1),
                     "peak": peak, "unit": "GB/s", "frac": round(gbytes / ms * 1e3 / peak, 4),
                     "algorithmic_bytes_per_launch": int(gbytes * 1e9)},
@@ -740,6 +743,7 @@ def main():
     ap.add_argument("--workload", default="csr65536", choices=["csr65536", "precision", "gnn", "batched", "selector"])
     ap.add_argument("--precision-layouts", default="uniform,clustered")
     ap.add_argument("--gnn-graphs", type=int, default=512)
+    ap.add_argument("--gat", action="store_true", help="gnn workload with the row softmax (GAT-style chain)")
     ap.add_argument("--selector-train", type=int, default=2000)
     ap.add_argument("--selector-test", type=int, default=200)
     ap.add_argument("--selector-steps", type=int, default=6000)

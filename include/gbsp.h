@@ -260,11 +260,22 @@ int sddmm_csr_batched(int G, const gbsp_csr *S, const gbsp_dense *X, const gbsp_
 typedef struct gbsp_gnn_plan gbsp_gnn_plan;
 int gbsp_gnn_plan_create(int G, const gbsp_csr *S, const gbsp_dense *H, float *const *E, gbsp_dense *O,
                          int32_t edges_per_tile, void *stream, gbsp_gnn_plan **out);
+/* GAT-style form (flags GBSP_GNN_SOFTMAX; the attention layer the paper names as the
+ * SDDMM -> SpMM use case): between the two products each row's scores are normalised,
+ *   alpha_ij = exp(E_ij - m_i) / sum_j exp(E_ij - m_i),  m_i = max_j E_ij  (stored entries),
+ * O_g = alpha H_g, and E[g] receives alpha.  The kernel keeps, per lane group, a running
+ * maximum, sum and accumulator (online softmax) and merges the groups at each row's end;
+ * exp is expf.  Rows without entries give zero O rows.  gbsp_gnn_plan_create is the
+ * flags = 0 form; gnn_gat_batched the one-shot softmax form. */
+#define GBSP_GNN_SOFTMAX 1
+int gbsp_gnn_plan_create_ex(int G, const gbsp_csr *S, const gbsp_dense *H, float *const *E, gbsp_dense *O,
+                            int32_t edges_per_tile, int32_t flags, void *stream, gbsp_gnn_plan **out);
 int gbsp_gnn_plan_execute(const gbsp_gnn_plan *plan, void *stream);
 int gbsp_gnn_plan_info(const gbsp_gnn_plan *plan, int64_t *info, int n);
 void gbsp_gnn_plan_destroy(gbsp_gnn_plan *plan);
 int gnn_sddmm_spmm_batched(int G, const gbsp_csr *S, const gbsp_dense *H, float *const *E, gbsp_dense *O,
                            void *stream);
+int gnn_gat_batched(int G, const gbsp_csr *S, const gbsp_dense *H, float *const *E, gbsp_dense *O, void *stream);
 
 /* ---- kernel selection: features, autotuner, MLP ------------------------------------------- */
 

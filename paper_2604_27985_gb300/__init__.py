@@ -20,6 +20,7 @@ from .ops import (  # noqa: F401
     variant_options,
     GnnPlan,
     gnn_sddmm_spmm_batched,
+    gnn_gat_batched,
     TcPlan,
     csr_validate,
     launch_count,

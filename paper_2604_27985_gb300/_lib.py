@@ -77,6 +77,10 @@ def _load() -> ctypes.CDLL:
         "gbsp_gnn_plan_info": [P, ctypes.POINTER(I64), I],
         "gnn_sddmm_spmm_batched": [I, ctypes.POINTER(Csr), ctypes.POINTER(Dense), ctypes.POINTER(P),
                                    ctypes.POINTER(Dense), P],
+        "gbsp_gnn_plan_create_ex": [I, ctypes.POINTER(Csr), ctypes.POINTER(Dense), ctypes.POINTER(P),
+                                    ctypes.POINTER(Dense), ctypes.c_int32, ctypes.c_int32, P, ctypes.POINTER(P)],
+        "gnn_gat_batched": [I, ctypes.POINTER(Csr), ctypes.POINTER(Dense), ctypes.POINTER(P), ctypes.POINTER(Dense),
+                            P],
         "gbsp_variant_opts": [I, ctypes.POINTER(Opts)],
         "gbsp_features": [ctypes.POINTER(Csr), I64, ctypes.c_int32, P, P],
         "gbsp_feature_norm": [P, I, P, P],

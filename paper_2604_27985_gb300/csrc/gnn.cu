@@ -11,6 +11,12 @@
 // edge's E value, reduced across the lane group by an xor butterfly) and the accumulation
 // E_ij * H_j into O_i, so H_j is read once per edge.  The launch (and the ticket reset) is
 // recorded once into a CUDA graph and replayed per execution.
+//
+// The GAT-style form (GBSP_GNN_SOFTMAX) puts a softmax over each row's scores between the
+// two products: alpha_ij = exp(E_ij - max_k E_ik) / sum_k exp(E_ik - max_k E_ik), O_i =
+// sum_j alpha_ij H_j, and E receives alpha.  It keeps the single gather per edge with an
+// online softmax: each lane group folds its edges into a running sum and accumulator
+// against a reference score, and the groups' states are merged at the row's end.
 #include <mutex>
 #include <vector>
 
@@ -81,12 +87,73 @@ __device__ __forceinline__ void gnn_step(const uint4 *Hv, int64_t ldv, const boo
     }
 }
 
+// The softmax form of a group step (the GAT-style chain).  Scores are kept in base-2 units,
+// z = e log2(e), so that every weight is one exp2f.  Each edge is folded in as soon as its
+// score is known, against the group's reference m: acc += 2^(z - m) H_j, l += 2^(z - m).
+// m is the first score of the row and moves up (rescaling acc and l by 2^(m - m')) only when
+// a score exceeds it by more than kLazy, so weights stay below 2^kLazy and the rescale is
+// rare; softmax does not depend on the reference, so the result is the same.  Lane L also
+// collects, by one shuffle per edge, the score of the chunk's entry L.
+constexpr float kLazy = 12.f;
+
+template <int LPN, int VPL, int U>
+__device__ __forceinline__ void gnn_step_softmax(const uint4 *Hv, int64_t ldv, const bool (&colok)[VPL], int c,
+                                                 float s, int q, int cnt, int sub, int lane,
+                                                 const float (&x)[VPL][8], float (&acc)[VPL][8], float &m, float &l,
+                                                 float &mine) {
+    constexpr int G = 32 / LPN;
+    uint4 raw[U][VPL];
+    float sj[U];
+    bool ok[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int idx = q + u * G + sub;
+        const int cj = __shfl_sync(FULL, c, idx & 31);
+        sj[u] = __shfl_sync(FULL, s, idx & 31);
+        ok[u] = idx < cnt;
+        const uint4 *rp = Hv + (int64_t)cj * ldv;
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) raw[u][v] = (ok[u] && colok[v]) ? __ldg(rp + v * LPN) : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        float f[VPL][8];
+        float2 d2 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) {
+            BF16::unpack(raw[u][v], f[v]);
+            dot2(x[v], f[v], d2);
+        }
+        float dot = d2.x + d2.y;
+#pragma unroll
+        for (int off = LPN / 2; off >= 1; off >>= 1) dot += __shfl_xor_sync(FULL, dot, off);
+        const float z = sj[u] * dot * 1.4426950408889634f;
+        const int rel = lane - (q + u * G);  // the chunk entry this lane collects, if in this step
+        const float zg = __shfl_sync(FULL, z, (rel & (G - 1)) * LPN);
+        if (rel >= 0 && rel < G) mine = zg;
+        if (!ok[u]) continue;
+        if (z > m + kLazy) {  // also the row's first edge, while m is -inf
+            const float r = exp2f(m - z);
+            l *= r;
+#pragma unroll
+            for (int v = 0; v < VPL; ++v)
+#pragma unroll
+                for (int t = 0; t < 8; ++t) acc[v][t] *= r;
+            m = z;
+        }
+        const float w = exp2f(z - m);
+        l += w;
+#pragma unroll
+        for (int v = 0; v < VPL; ++v) axpy2(w, f[v], acc[v]);
+    }
+}
+
 // The rows [r0, r1) (at most 63) of one graph, one after another, with LPN lanes per edge
 // and VPL 16-byte BF16 vectors (8 features each) per lane.  The tile's row pointers sit in
 // two registers per lane; the next row's first 32 column indices and values and its H row
 // are loaded while the current row computes.  Full steps take U edges per group; the rest
 // of a chunk goes one edge per group, so a row with a single edge costs one step.
-template <int LPN, int VPL, int U>
+template <int LPN, int VPL, int U, bool SOFTMAX>
 __device__ __forceinline__ void gnn_tile(const GraphDesc &g, int r0, int r1, int lane) {
     constexpr int G = 32 / LPN;
     constexpr int STEP = G * U;
@@ -134,6 +201,7 @@ __device__ __forceinline__ void gnn_tile(const GraphDesc &g, int r0, int r1, int
                 if (colok[v]) xn[v] = __ldg(Hv + (int64_t)(row + 1) * ldv + v * LPN);
         }
         float x[VPL][8], acc[VPL][8];
+        float m = -INFINITY, l = 0.f, mine = 0.f;  // softmax: the group's reference and sum; this lane's score
 #pragma unroll
         for (int v = 0; v < VPL; ++v) {
             BF16::unpack(xraw[v], x[v]);
@@ -151,11 +219,37 @@ __device__ __forceinline__ void gnn_tile(const GraphDesc &g, int r0, int r1, int
             }
             const int cnt = (int)min((int64_t)32, p1 - base);
             int q = 0;
+            if constexpr (SOFTMAX) {
 #pragma unroll 1
-            for (; q + STEP <= cnt; q += STEP)
-                gnn_step<LPN, VPL, U>(Hv, ldv, colok, c, s, q, cnt, sub, sl, x, acc, g.E, base);
+                for (; q + STEP <= cnt; q += STEP)
+                    gnn_step_softmax<LPN, VPL, U>(Hv, ldv, colok, c, s, q, cnt, sub, lane, x, acc, m, l, mine);
 #pragma unroll 1
-            for (; q < cnt; q += G) gnn_step<LPN, VPL, 1>(Hv, ldv, colok, c, s, q, cnt, sub, sl, x, acc, g.E, base);
+                for (; q < cnt; q += G)
+                    gnn_step_softmax<LPN, VPL, 1>(Hv, ldv, colok, c, s, q, cnt, sub, lane, x, acc, m, l, mine);
+                if (base + 32 < p1) g.E[base + lane] = mine;  // a later chunk follows: park the scores in E
+            } else {
+#pragma unroll 1
+                for (; q + STEP <= cnt; q += STEP)
+                    gnn_step<LPN, VPL, U>(Hv, ldv, colok, c, s, q, cnt, sub, sl, x, acc, g.E, base);
+#pragma unroll 1
+                for (; q < cnt; q += G)
+                    gnn_step<LPN, VPL, 1>(Hv, ldv, colok, c, s, q, cnt, sub, sl, x, acc, g.E, base);
+            }
+        }
+        float row_max = 0.f, inv_sum = 0.f;
+        if constexpr (SOFTMAX) {  // the groups' states merged: one maximum, rescaled sums
+            row_max = m;
+#pragma unroll
+            for (int off = LPN; off < 32; off <<= 1) row_max = fmaxf(row_max, __shfl_xor_sync(FULL, row_max, off));
+            const float f = m == -INFINITY ? 0.f : exp2f(m - row_max);
+            l *= f;
+#pragma unroll
+            for (int v = 0; v < VPL; ++v)
+#pragma unroll
+                for (int t = 0; t < 8; ++t) acc[v][t] *= f;
+#pragma unroll
+            for (int off = LPN; off < 32; off <<= 1) l += __shfl_xor_sync(FULL, l, off);
+            inv_sum = l > 0.f ? 1.0f / l : 0.f;
         }
 #pragma unroll
         for (int off = LPN; off < 32; off <<= 1)
@@ -163,6 +257,18 @@ __device__ __forceinline__ void gnn_tile(const GraphDesc &g, int r0, int r1, int
             for (int v = 0; v < VPL; ++v)
 #pragma unroll
                 for (int t = 0; t < 8; ++t) acc[v][t] += __shfl_xor_sync(FULL, acc[v][t], off);
+        if constexpr (SOFTMAX) {
+#pragma unroll
+            for (int v = 0; v < VPL; ++v)
+#pragma unroll
+                for (int t = 0; t < 8; ++t) acc[v][t] *= inv_sum;
+            // the weights: the last chunk's scores are in registers, earlier chunks' in E (each
+            // lane reads back what it stored)
+            const int64_t last = p1 > p0 ? p0 + ((p1 - p0 - 1) & ~(int64_t)31) : p0;  // the last chunk's start
+            int64_t p = p0 + lane;
+            for (; p < last; p += 32) g.E[p] = exp2f(g.E[p] - row_max) * inv_sum;
+            if (p < p1) g.E[p] = exp2f(mine - row_max) * inv_sum;
+        }
         if (lane < LPN) {
 #pragma unroll
             for (int v = 0; v < VPL; ++v) {
@@ -185,6 +291,7 @@ __device__ __forceinline__ void gnn_tile(const GraphDesc &g, int r0, int r1, int
     }
 }
 
+template <bool SOFTMAX>
 __global__ void __launch_bounds__(256, 3) gnn_kernel(const GnnArgs a) {
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -194,12 +301,14 @@ __global__ void __launch_bounds__(256, 3) gnn_kernel(const GnnArgs a) {
         if (t >= (unsigned)a.ntiles) return;
         const Tile tile = a.tiles[t];
         const GraphDesc g = a.graphs[tile.graph];
+        // The softmax form takes fewer edges per group step (2 and 1 instead of 4 and 2): its
+        // steps hold more live state, and this keeps it at three CTAs per SM without spills.
         if (g.N <= 64)
-            gnn_tile<8, 1, 4>(g, tile.row0, tile.row1, lane);
+            gnn_tile<8, 1, SOFTMAX ? 2 : 4, SOFTMAX>(g, tile.row0, tile.row1, lane);
         else if (g.N <= 128)
-            gnn_tile<8, 2, 2>(g, tile.row0, tile.row1, lane);
+            gnn_tile<8, 2, SOFTMAX ? 1 : 2, SOFTMAX>(g, tile.row0, tile.row1, lane);
         else
-            gnn_tile<16, 2, 2>(g, tile.row0, tile.row1, lane);
+            gnn_tile<16, 2, SOFTMAX ? 1 : 2, SOFTMAX>(g, tile.row0, tile.row1, lane);
     }
 }
 
@@ -235,10 +344,13 @@ void gnn_free(gbsp_gnn_plan *p) {
 
 }  // namespace
 
-GBSP_EXPORT int gbsp_gnn_plan_create(int G, const gbsp_csr *S, const gbsp_dense *H, float *const *E,
-                                     gbsp_dense *O, int32_t edges_per_tile, void *stream, gbsp_gnn_plan **out) {
+GBSP_EXPORT int gbsp_gnn_plan_create_ex(int G, const gbsp_csr *S, const gbsp_dense *H, float *const *E,
+                                        gbsp_dense *O, int32_t edges_per_tile, int32_t flags, void *stream,
+                                        gbsp_gnn_plan **out) {
     if (!out) return fail(GBSP_ERR_INVALID_ARG, "gnn plan: null output");
     *out = nullptr;
+    if (flags & ~GBSP_GNN_SOFTMAX) return fail(GBSP_ERR_INVALID_ARG, "gnn plan: unknown flags %d", flags);
+    const bool softmax = (flags & GBSP_GNN_SOFTMAX) != 0;
     if (G < 0 || (G > 0 && (!S || !H || !E || !O))) return fail(GBSP_ERR_INVALID_ARG, "gnn plan: bad arrays");
     if (edges_per_tile <= 0) edges_per_tile = 512;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -305,7 +417,10 @@ GBSP_EXPORT int gbsp_gnn_plan_create(int G, const gbsp_csr *S, const gbsp_dense 
     }
     // record: ticket reset + one persistent launch
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gnn_kernel, 256, 0);
+    if (softmax)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gnn_kernel<true>, 256, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gnn_kernel<false>, 256, 0);
     const int nblocks = sm_count() * (per_sm < 1 ? 1 : per_sm);
     GnnArgs args{p->d_graphs, p->d_tiles, p->ntiles, p->d_ticket};
     if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
@@ -316,7 +431,12 @@ GBSP_EXPORT int gbsp_gnn_plan_create(int G, const gbsp_csr *S, const gbsp_dense 
     bool okc = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (okc) {
         cudaMemsetAsync(p->d_ticket, 0, sizeof(unsigned), cap);
-        if (p->ntiles > 0) gnn_kernel<<<nblocks, 256, 0, cap>>>(args);
+        if (p->ntiles > 0) {
+            if (softmax)
+                gnn_kernel<true><<<nblocks, 256, 0, cap>>>(args);
+            else
+                gnn_kernel<false><<<nblocks, 256, 0, cap>>>(args);
+        }
         okc = cudaStreamEndCapture(cap, &p->graph) == cudaSuccess;
     }
     okc = okc && cudaGraphInstantiate(&p->exec, p->graph, 0) == cudaSuccess;
@@ -349,14 +469,33 @@ GBSP_EXPORT int gbsp_gnn_plan_info(const gbsp_gnn_plan *p, int64_t *info, int n)
 
 GBSP_EXPORT void gbsp_gnn_plan_destroy(gbsp_gnn_plan *p) { gnn_free(p); }
 
-GBSP_EXPORT int gnn_sddmm_spmm_batched(int G, const gbsp_csr *S, const gbsp_dense *H, float *const *E,
-                                       gbsp_dense *O, void *stream) {
+GBSP_EXPORT int gbsp_gnn_plan_create(int G, const gbsp_csr *S, const gbsp_dense *H, float *const *E,
+                                     gbsp_dense *O, int32_t edges_per_tile, void *stream, gbsp_gnn_plan **out) {
+    return gbsp_gnn_plan_create_ex(G, S, H, E, O, edges_per_tile, 0, stream, out);
+}
+
+namespace {
+
+int gnn_one_shot(int G, const gbsp_csr *S, const gbsp_dense *H, float *const *E, gbsp_dense *O, int32_t flags,
+                 void *stream) {
     gbsp_gnn_plan *p = nullptr;
-    int st = gbsp_gnn_plan_create(G, S, H, E, O, 0, stream, &p);
+    int st = gbsp_gnn_plan_create_ex(G, S, H, E, O, 0, flags, stream, &p);
     if (st) return st;
     st = gbsp_gnn_plan_execute(p, stream);
     if (!st && cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess)
         st = check_launch("gnn batched");
     gnn_free(p);
     return st ? st : ok();
+}
+
+}  // namespace
+
+GBSP_EXPORT int gnn_sddmm_spmm_batched(int G, const gbsp_csr *S, const gbsp_dense *H, float *const *E,
+                                       gbsp_dense *O, void *stream) {
+    return gnn_one_shot(G, S, H, E, O, 0, stream);
+}
+
+GBSP_EXPORT int gnn_gat_batched(int G, const gbsp_csr *S, const gbsp_dense *H, float *const *E, gbsp_dense *O,
+                                void *stream) {
+    return gnn_one_shot(G, S, H, E, O, GBSP_GNN_SOFTMAX, stream);
 }

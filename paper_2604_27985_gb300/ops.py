@@ -226,13 +226,16 @@ def _gnn_arrays(graphs):
 
 class GnnPlan:
     """Batched SDDMM -> SpMM chain over many graphs as one persistent launch replayed from a
-    CUDA graph (gbsp_gnn_plan_create).  ``execute()`` fills every graph's E and O."""
+    CUDA graph (gbsp_gnn_plan_create_ex).  ``execute()`` fills every graph's E and O; with
+    ``softmax=True`` each row's scores are normalised between the two products (GAT-style)
+    and E receives the weights."""
 
-    def __init__(self, graphs, edges_per_tile=0, stream=None):
+    def __init__(self, graphs, edges_per_tile=0, softmax=False, stream=None):
         self._keep = graphs  # the plan holds raw pointers into these tensors
         G, S, Hd, E, Od = _gnn_arrays(graphs)
         h = ctypes.c_void_p()
-        check(lib.gbsp_gnn_plan_create(G, S, Hd, E, Od, int(edges_per_tile), _stream(stream), ctypes.byref(h)))
+        check(lib.gbsp_gnn_plan_create_ex(G, S, Hd, E, Od, int(edges_per_tile), 1 if softmax else 0, _stream(stream),
+                                          ctypes.byref(h)))
         self._h = h
 
     def execute(self, stream=None) -> None:
@@ -259,6 +262,12 @@ def gnn_sddmm_spmm_batched(graphs, stream=None) -> None:
     """One-shot batched chain (creates, runs and destroys a plan; synchronises)."""
     G, S, Hd, E, Od = _gnn_arrays(graphs)
     check(lib.gnn_sddmm_spmm_batched(G, S, Hd, E, Od, _stream(stream)))
+
+
+def gnn_gat_batched(graphs, stream=None) -> None:
+    """One-shot GAT-style chain: scores, row softmax into E, O = E H (synchronises)."""
+    G, S, Hd, E, Od = _gnn_arrays(graphs)
+    check(lib.gnn_gat_batched(G, S, Hd, E, Od, _stream(stream)))
 
 
 # ---- kernel selection ------------------------------------------------------------------------

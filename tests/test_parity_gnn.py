@@ -5,6 +5,12 @@ Per graph: E = S o (H H^T) on the pattern of S (Eq. 2 with X = Y = H), then O = 
 FP32 tolerance (1e-5 of sum |s||h_i||h_j|).  O is held to the BF16 tolerance (1e-2) of a
 scale that also carries E's own error, sum_j (|E_ij| + scale(E_ij)) |H_j|, and to its
 rounding: |O - O_ref| <= 2^-8 |O_ref| + 1e-5 * that scale.
+
+The GAT-style form (softmax of each row's scores between the products) is held per row:
+a weight's relative error is at most twice the scores' error (1e-5 of the row's largest
+score scale, once for the entry and once through the normaliser) plus the FP32 rounding of
+exp2, the row's sum (deg terms) and the division; O's error is that times sum_j alpha_ij
+|H_j|, plus FP32 accumulation and BF16 rounding.
 """
 import numpy as np
 import pytest
@@ -138,3 +144,80 @@ def test_gnn_batch_configuration_sampled(gb):
         A, sv, Hd = host[i]
         d = devs[i]
         check_graph(A, sv, Hd, d[5].cpu().numpy(), d[4].float().cpu().numpy())
+
+
+# ---- GAT-style chain: softmax of each row's scores between SDDMM and SpMM ----------------------
+
+def check_gat(A, sv, Hd, E_gpu, O_gpu):
+    """alpha (E_gpu) against the oracle's row softmax of the FP64 scores, relative to a row
+    tolerance that carries the scores' FP32 error (1e-5 of their scale, twice: the entry and
+    the row's normaliser); O against alpha H with that error and BF16 rounding."""
+    alpha, O_ref, sO = oracle.gat_chain(A.rowptr, A.colidx, sv, Hd)
+    _, sE = oracle.sddmm(A.rowptr, A.colidx, sv, Hd, Hd)
+    lens = A.row_lengths()
+    row_scale = np.zeros(A.M)
+    nz = lens > 0
+    row_scale[nz] = np.maximum.reduceat(sE, A.rowptr[:-1][nz])
+    tol_row = 2e-5 * row_scale + 1e-6 + lens * 2.0**-24
+    tol_e = np.repeat(tol_row, lens)
+    assert np.all(np.abs(E_gpu - alpha) <= tol_e * alpha + 1e-7)
+    err = np.abs(O_gpu.astype(np.float64) - O_ref)
+    assert np.all(err <= 2.0**-8 * np.abs(O_ref) + (tol_row[:, None] + 1e-5) * sO + 1e-30)
+    assert np.all(O_gpu[~nz] == 0)
+
+
+@pytest.mark.parametrize("one_shot", [False, True])
+def test_gat_chain_random(gb, one_shot):
+    graphs = small_graphs(511)
+    host, devs = build_batch(graphs, 512)
+    if one_shot:
+        gb.gnn_gat_batched(devs)
+    else:
+        plan = gb.GnnPlan(devs, softmax=True)
+        plan.execute()
+        plan.execute()  # replay: E is overwritten with the same weights
+    import torch
+
+    torch.cuda.synchronize()
+    for (A, sv, Hd), d in zip(host, devs):
+        check_gat(A, sv, Hd, d[5].cpu().numpy(), d[4].float().cpu().numpy())
+
+
+def test_gat_chain_rows_and_special_cases(gb):
+    """Empty rows, single-edge rows (weight exactly 1), rows longer than a 32-edge chunk,
+    all-zero scores (weights 1/deg), and every width layout."""
+    import torch
+
+    rng = np.random.default_rng(513)
+    graphs = []
+    for k, N in enumerate((64, 128, 256, 8)):
+        n = 400
+        lengths = rng.integers(0, 6, n)
+        lengths[:40] = 0
+        lengths[40:80] = 1
+        lengths[80:90] = rng.integers(33, 120, 10)
+        graphs.append((gen.csr_from_lengths(lengths, n, seed=514 + k), N))
+    host, devs = build_batch(graphs, 515)
+    # one graph with zero values: every score 0, weights 1 / deg
+    A0, N0 = graphs[0]
+    devs[0] = (devs[0][0], devs[0][1], torch.zeros(A0.nnz, device="cuda"), *devs[0][3:])
+    host[0] = (A0, np.zeros(A0.nnz, np.float32), host[0][2])
+    gb.gnn_gat_batched(devs)
+    torch.cuda.synchronize()
+    for (A, sv, Hd), d in zip(host, devs):
+        E = d[5].cpu().numpy()
+        check_gat(A, sv, Hd, E, d[4].float().cpu().numpy())
+        single = np.repeat(A.row_lengths() == 1, A.row_lengths())
+        assert np.all(E[single] == 1.0)
+    lens0 = host[0][0].row_lengths()
+    want = np.repeat(np.where(lens0 > 0, 1.0 / np.maximum(lens0, 1), 0), lens0).astype(np.float32)
+    assert np.array_equal(devs[0][5].cpu().numpy(), want)
+
+
+def test_gat_plan_rejects_unknown_flags(gb):
+    import ctypes
+
+    from paper_2604_27985_gb300._lib import lib
+
+    h = ctypes.c_void_p()
+    assert lib.gbsp_gnn_plan_create_ex(0, None, None, None, None, 0, 2, None, ctypes.byref(h)) == -1
