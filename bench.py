@@ -537,6 +537,68 @@ def run_gnn(args):
           gpu_launches_per_step=int(launches))
 
 
+def run_sweep(args):
+    """The plain-FP32 scale / sparsity sweep: 65,536^2 at 99% and 1,048,576^2 at 99.99%
+    (about 110M nonzeros; 65,536^2 at 90% too with --sweep-dense, whose generation takes
+    minutes), uniform and power-law rows; SpMM at N in {32, 64, 128} and SDDMM at Kd in
+    {32, 128}, each with the library's automatic variant.  Every matrix's CSR arrays exceed
+    L2.  One JSON line: a point per (matrix, op, width) with its time, GFLOP/s and the
+    gather-model fraction of the HBM peak; value = all points' FLOPs over their summed time."""
+    import torch
+
+    import paper_2604_27985_gb300 as gb
+
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = peaks()
+    mats = [(65536, 0.99, "uniform", 1001), (65536, 0.99, "powerlaw", 1002),
+            (1048576, 0.9999, "uniform", 1003), (1048576, 0.9999, "powerlaw", 1004)]
+    if args.sweep_dense:
+        mats += [(65536, 0.9, "uniform", 1005), (65536, 0.9, "powerlaw", 1006)]
+    points, flop_sum, ms_sum, launches = [], 0.0, 0.0, 0
+    for n, sp, layout, seed in mats:
+        A = (gen.csr_uniform if layout == "uniform" else gen.csr_powerlaw)(n, n, sp, seed=seed)
+        rp, ci, v = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.colidx, A.vals))
+        g = torch.Generator(device=dev)
+        g.manual_seed(seed)
+        for op, widths in (("spmm", (32, 64, 128)), ("sddmm", (32, 128))):
+            for w in widths:
+                if op == "spmm":
+                    Bd = torch.randn((n, w), generator=g, device=dev)
+                    C = torch.empty((n, w), device=dev)
+                    fn = lambda: gb.spmm(rp, ci, v, Bd, out=C, stream=stream)
+                    nbytes = gather_bytes_spmm(A.nnz, n, w)
+                else:
+                    Xd = torch.randn((n, w), generator=g, device=dev)
+                    Yd = torch.randn((n, w), generator=g, device=dev)
+                    out = torch.empty(A.nnz, device=dev)
+                    fn = lambda: gb.sddmm(rp, ci, v, Xd, Yd, out=out, stream=stream)
+                    nbytes = gather_bytes_sddmm(A.nnz, n, w)
+                l0 = gb.launch_count()
+                ms = _event_ms(fn, args.steps, args.warmup, stream)
+                launches += gb.launch_count() - l0
+                f = 2.0 * A.nnz * w
+                flop_sum += f
+                ms_sum += ms
+                points.append({"n": n, "sparsity": sp, "rows": layout, "op": op, "width": w, "nnz": A.nnz,
+                               "ms": round(ms, 4), "gflops": round(f / ms / 1e6, 1),
+                               "gather_gbs": round(nbytes / ms / 1e6, 1),
+                               "frac": round(nbytes / ms / 1e6 / peak, 4)})
+                del fn
+        del A, rp, ci, v
+        torch.cuda.empty_cache()
+    _line("SpMM & SDDMM GFLOP/s (2*nnz*N) over the plain-FP32 scale/sparsity sweep", flop_sum / ms_sum / 1e6,
+          "GFLOP/s", ms_sum, args, "f32",
+          {"workload": "65536^2 at 99% and 1048576^2 at 99.99%" + (" and 65536^2 at 90%" if args.sweep_dense else "")
+                       + ", uniform and power-law rows (Zipf 1.5, cap 4096), values U[-1,1]; SpMM N 32/64/128, "
+                       "SDDMM Kd 32/128, dense operands N(0,1); automatic variant; CSR arrays larger than L2",
+           "points": points},
+          roofline={"bound": "hbm", "kernel": "spmm / sddmm, gather model", "peak": peak, "peak_kind": peak_kind,
+                    "unit": "GB/s", "frac_min": min(p["frac"] for p in points),
+                    "frac_max": max(p["frac"] for p in points)},
+          gpu_launches=int(launches))
+
+
 def run_batched(args):
     """Grouped SpMM and SDDMM over the 512 graphs of the batched configuration (BF16 H of
     width 64/128/256, FP32 outputs): persistent launches (one per lane-layout class) replayed
@@ -740,10 +802,11 @@ def main():
     ap.add_argument("--no-tuned", action="store_true")
     ap.add_argument("--e2e-chunks", type=int, default=8)
     ap.add_argument("--e2e-slots", type=int, default=4)
-    ap.add_argument("--workload", default="csr65536", choices=["csr65536", "precision", "gnn", "batched", "selector"])
+    ap.add_argument("--workload", default="csr65536", choices=["csr65536", "precision", "gnn", "batched", "selector", "sweep"])
     ap.add_argument("--precision-layouts", default="uniform,clustered")
     ap.add_argument("--gnn-graphs", type=int, default=512)
     ap.add_argument("--gat", action="store_true", help="gnn workload with the row softmax (GAT-style chain)")
+    ap.add_argument("--sweep-dense", action="store_true", help="sweep workload: add 65536^2 at 90%%")
     ap.add_argument("--selector-train", type=int, default=2000)
     ap.add_argument("--selector-test", type=int, default=200)
     ap.add_argument("--selector-steps", type=int, default=6000)
@@ -766,6 +829,8 @@ def main():
         run_batched(args)
     elif args.workload == "selector":
         run_selector(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     else:
         run_ours(args)
 
