@@ -543,14 +543,18 @@ def run_sweep(args):
     minutes), uniform and power-law rows; SpMM at N in {32, 64, 128} and SDDMM at Kd in
     {32, 128}, each with the library's automatic variant.  Every matrix's CSR arrays exceed
     L2.  One JSON line: a point per (matrix, op, width) with its time, GFLOP/s and the
-    gather-model fraction of the HBM peak; value = all points' FLOPs over their summed time."""
+    gather-model fraction of the HBM peak; value = all points' FLOPs over their summed time
+    (automatic variant).  SpMM points also time the shipped selector's variant choice."""
     import torch
 
     import paper_2604_27985_gb300 as gb
 
+    from paper_2604_27985_gb300 import selector as sel
+
     dev = torch.device("cuda")
     stream = torch.cuda.current_stream()
     peak, peak_kind = peaks()
+    model = sel.Selector.load()
     mats = [(65536, 0.99, "uniform", 1001), (65536, 0.99, "powerlaw", 1002),
             (1048576, 0.9999, "uniform", 1003), (1048576, 0.9999, "powerlaw", 1004)]
     if args.sweep_dense:
@@ -580,10 +584,19 @@ def run_sweep(args):
                 f = 2.0 * A.nnz * w
                 flop_sum += f
                 ms_sum += ms
-                points.append({"n": n, "sparsity": sp, "rows": layout, "op": op, "width": w, "nnz": A.nnz,
-                               "ms": round(ms, 4), "gflops": round(f / ms / 1e6, 1),
-                               "gather_gbs": round(nbytes / ms / 1e6, 1),
-                               "frac": round(nbytes / ms / 1e6 / peak, 4)})
+                pt = {"n": n, "sparsity": sp, "rows": layout, "op": op, "width": w, "nnz": A.nnz,
+                      "ms": round(ms, 4), "gflops": round(f / ms / 1e6, 1),
+                      "gather_gbs": round(nbytes / ms / 1e6, 1), "frac": round(nbytes / ms / 1e6 / peak, 4)}
+                if op == "spmm":  # the shipped selector's variant for this matrix and width (untimed choice)
+                    v_idx = model.choose(rp, ci, n, w, 0)
+                    kw = gb.variant_options(v_idx)
+                    ms_sel = _event_ms(lambda: gb.spmm(rp, ci, v, Bd, out=C, stream=stream, **kw), args.steps,
+                                       args.warmup, stream)
+                    ms_mp = _event_ms(lambda: gb.spmm(rp, ci, v, Bd, out=C, stream=stream, variant="merge"),
+                                      args.steps, args.warmup, stream)
+                    pt.update(selector_variant=v_idx, selector_options=kw, selector_ms=round(ms_sel, 4),
+                              selector_frac=round(nbytes / ms_sel / 1e6 / peak, 4), merge_ms=round(ms_mp, 4))
+                points.append(pt)
                 del fn
         del A, rp, ci, v
         torch.cuda.empty_cache()
