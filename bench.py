@@ -612,6 +612,64 @@ def run_sweep(args):
           gpu_launches=int(launches))
 
 
+def run_kbin(args):
+    """K-range-binned SpMM (gbsp_kbin_plan_*) on 1,048,576^2 at 99.99% (uniform and power-law
+    rows, the sweep's matrices), where B (128 to 512 MB at N = 32 to 128) exceeds L2: the
+    plan's passes over L2-sized B slices against the automatic row split and the merge path,
+    for slice budgets of 24, 48 (the default) and 96 MB.  One JSON line; value = the default
+    plan's GFLOP/s over all points (2*nnz*N over the summed time)."""
+    import torch
+
+    import paper_2604_27985_gb300 as gb
+
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = peaks()
+    points, flop_sum, ms_sum, launches = [], 0.0, 0.0, 0
+    for layout, seed in (("uniform", 1003), ("powerlaw", 1004)):
+        n = 1048576
+        A = (gen.csr_uniform if layout == "uniform" else gen.csr_powerlaw)(n, n, 0.9999, seed=seed)
+        rp, ci, v = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.colidx, A.vals))
+        g = torch.Generator(device=dev)
+        g.manual_seed(seed)
+        for N in (32, 64, 128):
+            Bd = torch.randn((n, N), generator=g, device=dev)
+            C = torch.empty((n, N), device=dev)
+            f = 2.0 * A.nnz * N
+            nbytes = gather_bytes_spmm(A.nnz, n, N)
+            pt = {"rows": layout, "N": N, "nnz": A.nnz,
+                  "rowsplit_ms": round(_event_ms(lambda: gb.spmm(rp, ci, v, Bd, out=C, stream=stream), args.steps,
+                                                 args.warmup, stream), 4),
+                  "merge_ms": round(_event_ms(lambda: gb.spmm(rp, ci, v, Bd, out=C, variant="merge", stream=stream),
+                                              args.steps, args.warmup, stream), 4)}
+            for mb in (24, 48, 96):
+                plan = gb.KbinPlan(rp, ci, v, n, N, slice_cols=(mb << 20) // (4 * N))
+                l0 = gb.launch_count()
+                ms = _event_ms(lambda: plan.execute(Bd, out=C, stream=stream), args.steps, args.warmup, stream)
+                if mb == 48:
+                    launches += gb.launch_count() - l0
+                    flop_sum += f
+                    ms_sum += ms
+                    pt.update(kbin_ms=round(ms, 4), slices=plan.info()["slices"], gflops=round(f / ms / 1e6, 1),
+                              gather_gbs=round(nbytes / ms / 1e6, 1), frac=round(nbytes / ms / 1e6 / peak, 4),
+                              c_partial_bytes=int((2 * plan.info()["slices"] - 1) * n * N * 4))
+                pt[f"kbin_{mb}mb_ms"] = round(ms, 4)
+                plan.close()
+            points.append(pt)
+            del Bd, C
+        del A, rp, ci, v
+        torch.cuda.empty_cache()
+    _line("K-binned SpMM GFLOP/s (2*nnz*N) with B larger than L2", flop_sum / ms_sum / 1e6, "GFLOP/s", ms_sum, args,
+          "f32",
+          {"workload": "1048576^2 at 99.99% (109,951,163 nonzeros), uniform and power-law rows, values U[-1,1]; "
+                       "B N(0,1) FP32 with N 32/64/128; default 48 MB B slices; CSR larger than L2",
+           "points": points},
+          roofline={"bound": "hbm", "kernel": "kbin_pass_kernel, gather model", "peak": peak,
+                    "peak_kind": peak_kind, "unit": "GB/s", "frac_min": min(p["frac"] for p in points),
+                    "frac_max": max(p["frac"] for p in points)},
+          gpu_launches=int(launches))
+
+
 def run_batched(args):
     """Grouped SpMM and SDDMM over the 512 graphs of the batched configuration (BF16 H of
     width 64/128/256, FP32 outputs): persistent launches (one per lane-layout class) replayed
@@ -815,7 +873,7 @@ def main():
     ap.add_argument("--no-tuned", action="store_true")
     ap.add_argument("--e2e-chunks", type=int, default=8)
     ap.add_argument("--e2e-slots", type=int, default=4)
-    ap.add_argument("--workload", default="csr65536", choices=["csr65536", "precision", "gnn", "batched", "selector", "sweep"])
+    ap.add_argument("--workload", default="csr65536", choices=["csr65536", "precision", "gnn", "batched", "selector", "sweep", "kbin"])
     ap.add_argument("--precision-layouts", default="uniform,clustered")
     ap.add_argument("--gnn-graphs", type=int, default=512)
     ap.add_argument("--gat", action="store_true", help="gnn workload with the row softmax (GAT-style chain)")
@@ -844,6 +902,8 @@ def main():
         run_selector(args)
     elif args.workload == "sweep":
         run_sweep(args)
+    elif args.workload == "kbin":
+        run_kbin(args)
     else:
         run_ours(args)
 

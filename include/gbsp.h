@@ -264,8 +264,9 @@ int gbsp_gnn_plan_create(int G, const gbsp_csr *S, const gbsp_dense *H, float *c
  * SDDMM -> SpMM use case): between the two products each row's scores are normalised,
  *   alpha_ij = exp(E_ij - m_i) / sum_j exp(E_ij - m_i),  m_i = max_j E_ij  (stored entries),
  * O_g = alpha H_g, and E[g] receives alpha.  The kernel keeps, per lane group, a running
- * maximum, sum and accumulator (online softmax) and merges the groups at each row's end;
- * exp is expf.  Rows without entries give zero O rows.  gbsp_gnn_plan_create is the
+ * sum and accumulator against a reference score (online softmax) and merges the groups at
+ * each row's end; the exponentials are exp2f of base-2 scaled scores.  Rows without entries
+ * give zero O rows.  gbsp_gnn_plan_create is the
  * flags = 0 form; gnn_gat_batched the one-shot softmax form. */
 #define GBSP_GNN_SOFTMAX 1
 int gbsp_gnn_plan_create_ex(int G, const gbsp_csr *S, const gbsp_dense *H, float *const *E, gbsp_dense *O,
@@ -276,6 +277,33 @@ void gbsp_gnn_plan_destroy(gbsp_gnn_plan *plan);
 int gnn_sddmm_spmm_batched(int G, const gbsp_csr *S, const gbsp_dense *H, float *const *E, gbsp_dense *O,
                            void *stream);
 int gnn_gat_batched(int G, const gbsp_csr *S, const gbsp_dense *H, float *const *E, gbsp_dense *O, void *stream);
+
+/* ---- K-range-binned SpMM (B larger than L2) ---------------------------------------------- */
+
+/* SpMM, Eq. 1, C = A B for FP32 A (M x K, CSR) and FP32 B (K x N), with A's columns cut into
+ * S slices of W consecutive indices (the 1.5D binning of A's nonzeros by K-range, Section
+ * III): pass s sums, for every row, the entries whose column lies in slice s, so its B
+ * gathers stay inside W rows of B (about 48 MB by default, held in L2).  Pass 0 writes C,
+ * later passes add to the rows with entries in their slice.  The result is Eq. 1's sum in
+ * slice order (FP32, deterministic).
+ *
+ * gbsp_kbin_plan_create checks A (gbsp_csr_validate's checks, and column indices
+ * non-decreasing within each row: GBSP_ERR_INVALID_CSR otherwise), chooses W (slice_cols, or
+ * for slice_cols = 0 the number of B rows of width N that fill 48 MB, at least 1024; capped
+ * at K; at most 4096 slices, GBSP_ERR_INVALID_ARG beyond) and stores, for every slice
+ * boundary and row, the first entry at or past it ((S + 1) x M int32 on the device).  It
+ * synchronises the stream.  The plan keeps A's pointers: the values may change between
+ * executions, the pattern and the allocations may not.
+ * gbsp_kbin_plan_execute: B float[K x N] (ld >= N), C float[M x N] (ld >= N, overwritten);
+ * N and both ld multiples of 4, B and C 16-byte aligned (GBSP_ERR_ALIGN otherwise); any N,
+ * not only the one W was sized for.  S launches on the stream (asynchronous); the current
+ * device must be the plan's.
+ * gbsp_kbin_plan_info fills {slices S, slice width W, rows M, nnz}. */
+typedef struct gbsp_kbin_plan gbsp_kbin_plan;
+int gbsp_kbin_plan_create(const gbsp_csr *A, int64_t N, int64_t slice_cols, void *stream, gbsp_kbin_plan **out);
+int gbsp_kbin_plan_execute(const gbsp_kbin_plan *plan, const gbsp_dense *B, gbsp_dense *C, void *stream);
+int gbsp_kbin_plan_info(const gbsp_kbin_plan *plan, int64_t *info, int n);
+void gbsp_kbin_plan_destroy(gbsp_kbin_plan *plan);
 
 /* ---- kernel selection: features, autotuner, MLP ------------------------------------------- */
 

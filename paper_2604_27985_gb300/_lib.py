@@ -81,6 +81,9 @@ def _load() -> ctypes.CDLL:
                                     ctypes.POINTER(Dense), ctypes.c_int32, ctypes.c_int32, P, ctypes.POINTER(P)],
         "gnn_gat_batched": [I, ctypes.POINTER(Csr), ctypes.POINTER(Dense), ctypes.POINTER(P), ctypes.POINTER(Dense),
                             P],
+        "gbsp_kbin_plan_create": [ctypes.POINTER(Csr), I64, I64, P, ctypes.POINTER(P)],
+        "gbsp_kbin_plan_execute": [P, ctypes.POINTER(Dense), ctypes.POINTER(Dense), P],
+        "gbsp_kbin_plan_info": [P, ctypes.POINTER(I64), I],
         "gbsp_variant_opts": [I, ctypes.POINTER(Opts)],
         "gbsp_features": [ctypes.POINTER(Csr), I64, ctypes.c_int32, P, P],
         "gbsp_feature_norm": [P, I, P, P],
@@ -107,6 +110,8 @@ def _load() -> ctypes.CDLL:
         fn.restype = I
     lib.gbsp_batch_plan_destroy.argtypes = [P]
     lib.gbsp_batch_plan_destroy.restype = None
+    lib.gbsp_kbin_plan_destroy.argtypes = [P]
+    lib.gbsp_kbin_plan_destroy.restype = None
     lib.gbsp_gnn_plan_destroy.argtypes = [P]
     lib.gbsp_gnn_plan_destroy.restype = None
     lib.gbsp_plan_destroy.argtypes = [P]
