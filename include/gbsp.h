@@ -282,7 +282,8 @@ int gnn_gat_batched(int G, const gbsp_csr *S, const gbsp_dense *H, float *const 
 
 /* SpMM, Eq. 1, C = A B for FP32 A (M x K, CSR) and FP32 B (K x N), with A's columns cut into
  * S slices of W consecutive indices (the 1.5D binning of A's nonzeros by K-range, Section
- * III): pass s sums, for every row, the entries whose column lies in slice s, so its B
+ * II-C and the column-range filter of Section III-A): pass s sums, for every row, the
+ * entries whose column lies in slice s, so its B
  * gathers stay inside W rows of B (about 48 MB by default, held in L2).  Pass 0 writes C,
  * later passes add to the rows with entries in their slice.  The result is Eq. 1's sum in
  * slice order (FP32, deterministic).

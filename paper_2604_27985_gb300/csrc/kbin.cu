@@ -6,16 +6,15 @@
 // stays resident in L2 (about 48 MB by default) while the pass runs.  Pass 0 writes C (zero
 // rows where a row has nothing in the slice); each later pass adds its part to the rows
 // that have entries in the slice (read, add, write of C).  This is the 1.5D idea of
-// binning A's nonzeros by K-range (Section III, the decomposition in which A is streamed
-// and X stays put), with the slice held in the GPU's L2 instead of a processor's memory.
+// binning A's nonzeros by K-range (Section II-C: A is streamed, each processor column keeps
+// one K-range of the dense operand; the routers of Section III-A filter A's entries by that
+// range), with the slice held in the GPU's L2 instead of a processor's memory.
 //
 // Because a row's column indices are sorted, its entries in slice s are one contiguous
 // range; the plan stores, per slice boundary and row, the first entry at or past that
 // boundary ((S + 1) x M int32, found by binary search), and uses the caller's rowptr /
 // colidx / vals in place.  Each pass is the row-split kernel's body (one warp per row,
 // vectorised gathers, lane groups reduced by xor butterflies) over that range.
-#include <cstdio>
-
 #include "spmm_launch.cuh"
 
 namespace gbsp {
