@@ -670,6 +670,81 @@ def run_kbin(args):
           gpu_launches=int(launches))
 
 
+def _event_ms_flushed(fn, steps, warmup, stream, flush):
+    """Mean CUDA-event time of fn with L2 flushed (a buffer larger than L2 rewritten) before
+    every call, outside the events."""
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    total = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / steps
+
+
+def run_hsp(args):
+    """Hyper-sparse SpMM (gbsp_hsp_plan_*): rows binned by length in one launch, against the
+    automatic row split and the merge path, on 1,048,576^2 at 99.9999% (about 1 entry per
+    row), 262,144^2 at 99.999% (about 2.6), 65,536^2 at 99.99% (about 6.6) and 262,144^2 at
+    99.99% with power-law rows (mean 26, most rows short); N 32 / 64 / 128.  These inputs
+    fit in L2, so L2 is flushed before every timed call.  One JSON line; value = the plan's
+    GFLOP/s over all points."""
+    import torch
+
+    import paper_2604_27985_gb300 as gb
+
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = peaks()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    mats = [(1048576, 0.999999, "uniform", 1007), (262144, 0.99999, "uniform", 1008),
+            (65536, 0.9999, "uniform", 1009), (262144, 0.9999, "powerlaw", 1010)]
+    points, flop_sum, ms_sum, launches = [], 0.0, 0.0, 0
+    for n, sp, layout, seed in mats:
+        A = (gen.csr_uniform if layout == "uniform" else gen.csr_powerlaw)(n, n, sp, seed=seed)
+        rp, ci, v = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.colidx, A.vals))
+        plan = gb.HspPlan(rp, ci, v, n)
+        g = torch.Generator(device=dev)
+        g.manual_seed(seed)
+        for N in (32, 64, 128):
+            Bd = torch.randn((n, N), generator=g, device=dev)
+            C = torch.empty((n, N), device=dev)
+            f = 2.0 * A.nnz * N
+            nbytes = gather_bytes_spmm(A.nnz, n, N)
+            t = lambda fn: round(_event_ms_flushed(fn, args.steps, args.warmup, stream, flush), 4)
+            l0 = gb.launch_count()
+            ms = _event_ms_flushed(lambda: plan.execute(Bd, out=C, stream=stream), args.steps, args.warmup, stream,
+                                   flush)
+            launches += (gb.launch_count() - l0) // (args.steps + args.warmup)
+            flop_sum += f
+            ms_sum += ms
+            points.append({"n": n, "sparsity": sp, "rows": layout, "N": N, "nnz": A.nnz, **plan.info(),
+                           "hsp_ms": round(ms, 4), "gflops": round(f / ms / 1e6, 1),
+                           "gather_gbs": round(nbytes / ms / 1e6, 1), "frac": round(nbytes / ms / 1e6 / peak, 4),
+                           "rowsplit_ms": t(lambda: gb.spmm(rp, ci, v, Bd, out=C, stream=stream)),
+                           "merge_ms": t(lambda: gb.spmm(rp, ci, v, Bd, out=C, variant="merge", stream=stream))})
+            del Bd, C
+        plan.close()
+        del A, rp, ci, v
+        torch.cuda.empty_cache()
+    _line("hyper-sparse SpMM GFLOP/s (2*nnz*N)", flop_sum / ms_sum / 1e6, "GFLOP/s", ms_sum, args, "f32",
+          {"workload": "1048576^2 at 99.9999%, 262144^2 at 99.999%, 65536^2 at 99.99% (uniform rows) and 262144^2 "
+                       "at 99.99% (power-law rows), values U[-1,1], B N(0,1) FP32, N 32/64/128",
+           "l2": "flushed before every timed call (256 MB written)", "points": points},
+          roofline={"bound": "hbm", "kernel": "hsp_kernel, gather model", "peak": peak, "peak_kind": peak_kind,
+                    "unit": "GB/s", "frac_min": min(p["frac"] for p in points),
+                    "frac_max": max(p["frac"] for p in points)},
+          gpu_launches_per_call=int(launches // max(1, len(points))))
+
+
 def run_batched(args):
     """Grouped SpMM and SDDMM over the 512 graphs of the batched configuration (BF16 H of
     width 64/128/256, FP32 outputs): persistent launches (one per lane-layout class) replayed
@@ -873,7 +948,7 @@ def main():
     ap.add_argument("--no-tuned", action="store_true")
     ap.add_argument("--e2e-chunks", type=int, default=8)
     ap.add_argument("--e2e-slots", type=int, default=4)
-    ap.add_argument("--workload", default="csr65536", choices=["csr65536", "precision", "gnn", "batched", "selector", "sweep", "kbin"])
+    ap.add_argument("--workload", default="csr65536", choices=["csr65536", "precision", "gnn", "batched", "selector", "sweep", "kbin", "hsp"])
     ap.add_argument("--precision-layouts", default="uniform,clustered")
     ap.add_argument("--gnn-graphs", type=int, default=512)
     ap.add_argument("--gat", action="store_true", help="gnn workload with the row softmax (GAT-style chain)")
@@ -904,6 +979,8 @@ def main():
         run_sweep(args)
     elif args.workload == "kbin":
         run_kbin(args)
+    elif args.workload == "hsp":
+        run_hsp(args)
     else:
         run_ours(args)
 

@@ -306,6 +306,28 @@ int gbsp_kbin_plan_execute(const gbsp_kbin_plan *plan, const gbsp_dense *B, gbsp
 int gbsp_kbin_plan_info(const gbsp_kbin_plan *plan, int64_t *info, int n);
 void gbsp_kbin_plan_destroy(gbsp_kbin_plan *plan);
 
+/* ---- hyper-sparse SpMM (rows binned by length) -------------------------------------------- */
+
+/* SpMM, Eq. 1, C = A B for FP32 A (M x K, CSR) and B (K x N), for matrices whose rows hold
+ * a few entries or none (past 99.9% sparsity; the weak spot the paper reports for its own
+ * design, Section IV-C, and its future work, Section V).  gbsp_hsp_plan_create checks A as
+ * gbsp_csr_validate does (GBSP_ERR_INVALID_CSR), reads the row lengths (synchronises the
+ * stream) and bins the rows: long rows (more than 32 entries) take one warp each as in the
+ * row split; short rows (1 to 32), sorted by length, take one lane group each (several rows
+ * per warp); empty rows get their zero C rows.  The plan keeps A's pointers (values may
+ * change between executions; the pattern and allocations may not) and the three row lists
+ * (M int32 on the device).
+ * gbsp_hsp_plan_execute: B float[K x N] (ld >= N), C float[M x N] (ld >= N, overwritten);
+ * N and both ld multiples of 4, B and C 16-byte aligned (GBSP_ERR_ALIGN otherwise).  One
+ * launch on the stream (asynchronous); each row's sum runs in its stored order within a
+ * short row, in the row split's order within a long row.
+ * gbsp_hsp_plan_info fills {long rows, short rows, empty rows, nnz}. */
+typedef struct gbsp_hsp_plan gbsp_hsp_plan;
+int gbsp_hsp_plan_create(const gbsp_csr *A, void *stream, gbsp_hsp_plan **out);
+int gbsp_hsp_plan_execute(const gbsp_hsp_plan *plan, const gbsp_dense *B, gbsp_dense *C, void *stream);
+int gbsp_hsp_plan_info(const gbsp_hsp_plan *plan, int64_t *info, int n);
+void gbsp_hsp_plan_destroy(gbsp_hsp_plan *plan);
+
 /* ---- kernel selection: features, autotuner, MLP ------------------------------------------- */
 
 /* The 24 SpMM variants the selector chooses among, as options for spmm_csr_ex:

@@ -21,6 +21,7 @@ from .ops import (  # noqa: F401
     GnnPlan,
     gnn_sddmm_spmm_batched,
     gnn_gat_batched,
+    HspPlan,
     KbinPlan,
     TcPlan,
     csr_validate,

@@ -84,6 +84,9 @@ def _load() -> ctypes.CDLL:
         "gbsp_kbin_plan_create": [ctypes.POINTER(Csr), I64, I64, P, ctypes.POINTER(P)],
         "gbsp_kbin_plan_execute": [P, ctypes.POINTER(Dense), ctypes.POINTER(Dense), P],
         "gbsp_kbin_plan_info": [P, ctypes.POINTER(I64), I],
+        "gbsp_hsp_plan_create": [ctypes.POINTER(Csr), P, ctypes.POINTER(P)],
+        "gbsp_hsp_plan_execute": [P, ctypes.POINTER(Dense), ctypes.POINTER(Dense), P],
+        "gbsp_hsp_plan_info": [P, ctypes.POINTER(I64), I],
         "gbsp_variant_opts": [I, ctypes.POINTER(Opts)],
         "gbsp_features": [ctypes.POINTER(Csr), I64, ctypes.c_int32, P, P],
         "gbsp_feature_norm": [P, I, P, P],
@@ -110,6 +113,8 @@ def _load() -> ctypes.CDLL:
         fn.restype = I
     lib.gbsp_batch_plan_destroy.argtypes = [P]
     lib.gbsp_batch_plan_destroy.restype = None
+    lib.gbsp_hsp_plan_destroy.argtypes = [P]
+    lib.gbsp_hsp_plan_destroy.restype = None
     lib.gbsp_kbin_plan_destroy.argtypes = [P]
     lib.gbsp_kbin_plan_destroy.restype = None
     lib.gbsp_gnn_plan_destroy.argtypes = [P]

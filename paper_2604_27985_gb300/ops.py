@@ -247,6 +247,44 @@ class KbinPlan:
             pass
 
 
+class HspPlan:
+    """Hyper-sparse SpMM plan of an FP32 CSR matrix (gbsp_hsp_plan_create): rows binned by
+    length (long rows one warp each, short rows one lane group each, empty rows zeroed) in
+    one launch.  ``execute(B)`` returns C = A B.  The plan keeps the tensors' pointers."""
+
+    def __init__(self, rowptr, colidx, vals, ncols, stream=None):
+        self._keep = (rowptr, colidx, vals)
+        self.M = rowptr.numel() - 1
+        self.K = int(ncols)
+        A = _csr(rowptr, colidx, vals, ncols)
+        h = ctypes.c_void_p()
+        check(lib.gbsp_hsp_plan_create(ctypes.byref(A), _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    def execute(self, B, out=None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.M, B.shape[1]), dtype=torch.float32, device=B.device)
+        b, c = _dense(B), _dense(out)
+        check(lib.gbsp_hsp_plan_execute(self._h, ctypes.byref(b), ctypes.byref(c), _stream(stream)))
+        return out
+
+    def info(self) -> dict:
+        arr = (ctypes.c_int64 * 4)()
+        check(lib.gbsp_hsp_plan_info(self._h, arr, 4))
+        return {"long_rows": arr[0], "short_rows": arr[1], "empty_rows": arr[2], "nnz": arr[3]}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib.gbsp_hsp_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def _gnn_arrays(graphs):
     """graphs: list of (rowptr, colidx, svals, H, O, E) CUDA tensors (H, O BF16; E float32)."""
     G = len(graphs)
