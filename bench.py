@@ -9,6 +9,12 @@ needed between steps.  Prints one JSON line.
 
 --impl reference times the FP64 CPU oracle on the host cores (a bounded row sample of the
 same workload per step) and prints the same line with "impl": "reference".
+
+The other rows of the hot path print one line each with --workload: precision (BF16 /
+E4M3 forms and the tensor-core plans on 16,384^2 at 90%), gnn (the 512-graph chain; --gat
+adds the row softmax), batched (grouped SpMM / SDDMM plans), selector (training, regret),
+sweep (the FP32 scale / sparsity sweep with the selector's choice), kbin (K-binned SpMM on
+1,048,576^2) and hsp (hyper-sparse SpMM).
 """
 from __future__ import annotations
 
