@@ -315,8 +315,9 @@ void gbsp_kbin_plan_destroy(gbsp_kbin_plan *plan);
  * stream) and bins the rows: long rows (more than 32 entries) take one warp each as in the
  * row split; short rows (1 to 32), sorted by length, take one lane group each (several rows
  * per warp); empty rows get their zero C rows.  The plan keeps A's pointers (values may
- * change between executions; the pattern and allocations may not) and the three row lists
- * (M int32 on the device).
+ * change between executions; the pattern and allocations may not), the long and empty
+ * row lists (int32) and a 16-byte record per short row {row, first entry, end, first
+ * column index} on the device.
  * gbsp_hsp_plan_execute: B float[K x N] (ld >= N), C float[M x N] (ld >= N, overwritten);
  * N and both ld multiples of 4, B and C 16-byte aligned (GBSP_ERR_ALIGN otherwise).  One
  * launch on the stream (asynchronous); each row's sum runs in its stored order within a

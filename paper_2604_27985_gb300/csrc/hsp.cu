@@ -7,7 +7,8 @@
 // reduction); short rows (1 to 32 entries), sorted by length so that the groups of a warp
 // finish together, get one lane group each (32 / LPN rows per warp, every group gathering
 // its own row's B rows, no cross-group reduction); empty rows get their zero C rows
-// stored.  One launch covers the three lists (consecutive block ranges, the column tile in
+// stored.  A short row is a 16-byte record {row, first entry, end, first column index}
+// (the pattern is fixed by the plan), so its first B gather starts right after one load.  One launch covers the three lists (consecutive block ranges, the column tile in
 // blockIdx.y), so every C row is written exactly once.
 #include <algorithm>
 #include <vector>
@@ -24,7 +25,8 @@ using spmm_detail::store_row;
 constexpr int kShortMax = 32;  // rows of at most this many entries take one lane group
 
 struct HspLists {
-    const int32_t *long_rows, *short_rows, *empty_rows;
+    const int32_t *long_rows, *empty_rows;
+    const int4 *short_recs;  // {row, p0, p1, colidx[p0]} per short row
     int32_t n_long, n_short, n_empty;
     int32_t b_long, b_short;  // block ranges: [0, b_long) long, then b_short short, then empty
 };
@@ -32,7 +34,7 @@ struct HspLists {
 // One short row per lane group: U entries at a time, every lane gathering its VPL vectors
 // of each entry's B row (the group's lanes read the same index and value: one broadcast).
 template <int LPN, int VPL, int U>
-__device__ __forceinline__ void short_row(const SpmmProblem &P, int64_t p0, int64_t p1, int col_base,
+__device__ __forceinline__ void short_row(const SpmmProblem &P, int64_t p0, int64_t p1, int c0, int col_base,
                                           float (&acc)[VPL][4]) {
     const float4 *Bv = static_cast<const float4 *>(P.B) + col_base / 4;
     const int64_t ldv = P.ldb / 4;
@@ -47,7 +49,7 @@ __device__ __forceinline__ void short_row(const SpmmProblem &P, int64_t p0, int6
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             ok[u] = p + u < p1;
-            c[u] = ok[u] ? __ldg(P.colidx + p + u) : 0;
+            c[u] = !ok[u] ? 0 : p + u == p0 ? c0 : __ldg(P.colidx + p + u);
             a[u] = ok[u] ? __ldg(vals + p + u) : 0.f;
         }
         float4 raw[U][VPL];
@@ -99,9 +101,9 @@ __global__ void __launch_bounds__(256) hsp_kernel(const SpmmProblem P, const Hsp
     if (b < L.b_short) {  // one lane group per short row
         const int64_t k = ((int64_t)b * 8 + warp) * G + lane / LPN;
         if (k >= L.n_short) return;
-        const int row = L.short_rows[k];
-        short_row<LPN, VPL, U>(P, P.rowptr[row], P.rowptr[row + 1], col_base, acc);
-        float *dst = P.C + (int64_t)row * P.ldc;
+        const int4 r = __ldg(L.short_recs + k);
+        short_row<LPN, VPL, U>(P, r.y, r.z, r.w, col_base, acc);
+        float *dst = P.C + (int64_t)r.x * P.ldc;
 #pragma unroll
         for (int v = 0; v < VPL; ++v) {
             const int col = col_base + v * LPN * EL::V;
@@ -114,6 +116,13 @@ __global__ void __launch_bounds__(256) hsp_kernel(const SpmmProblem P, const Hsp
     const int k = b * 8 + warp;  // one warp per empty row: its zero C row (this column tile)
     if (k >= L.n_empty) return;
     store_row<EL, LPN, VPL>(P.C + (int64_t)L.empty_rows[k] * P.ldc, acc, lane, col_base, P.N, 1.0f);
+}
+
+// recs[k].w = colidx[recs[k].y] (every short row has at least one entry)
+__global__ void hsp_first_col_kernel(int4 *recs, int32_t n, const int32_t *colidx) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride)
+        recs[k].w = colidx[recs[k].y];
 }
 
 template <int LPN, int VPL, int U>
@@ -171,7 +180,8 @@ struct gbsp_hsp_plan {
     const int32_t *rowptr, *colidx;
     const float *vals;
     int32_t n_long, n_short, n_empty;
-    int32_t *d_rows;  // long rows, then short rows by decreasing length, then empty rows
+    int32_t *d_rows;  // long rows, then empty rows
+    int4 *d_recs;     // short rows by decreasing length: {row, p0, p1, colidx[p0]}
 };
 
 namespace {
@@ -179,6 +189,7 @@ namespace {
 void hsp_free(gbsp_hsp_plan *p) {
     if (!p) return;
     cudaFree(p->d_rows);
+    cudaFree(p->d_recs);
     delete p;
 }
 
@@ -227,9 +238,11 @@ GBSP_EXPORT int gbsp_hsp_plan_create(const gbsp_csr *A, void *stream, gbsp_hsp_p
             by_len[len].push_back((int32_t)i);
     }
     std::vector<int32_t> rows(long_rows);
-    for (int len = kShortMax; len >= 1; --len) rows.insert(rows.end(), by_len[len].begin(), by_len[len].end());
-    const int32_t n_short = (int32_t)(rows.size() - long_rows.size());
     rows.insert(rows.end(), empty_rows.begin(), empty_rows.end());
+    std::vector<int4> recs;
+    for (int len = kShortMax; len >= 1; --len)
+        for (int32_t r : by_len[len]) recs.push_back(make_int4(r, rp[r], rp[r + 1], 0));
+    const int32_t n_short = (int32_t)recs.size();
 
     gbsp_hsp_plan *p = new gbsp_hsp_plan{};
     cudaGetDevice(&p->device);
@@ -253,6 +266,28 @@ GBSP_EXPORT int gbsp_hsp_plan_create(const gbsp_csr *A, void *stream, gbsp_hsp_p
             const int st = check_launch("hsp plan upload");
             hsp_free(p);
             return st ? st : fail(GBSP_ERR_CUDA, "hsp plan upload");
+        }
+    }
+    if (!recs.empty()) {
+        if (cudaMalloc(&p->d_recs, sizeof(int4) * recs.size()) != cudaSuccess) {
+            cudaGetLastError();
+            hsp_free(p);
+            return fail(GBSP_ERR_OOM, "hsp plan: allocation failed");
+        }
+        if (cudaMemcpy(p->d_recs, recs.data(), sizeof(int4) * recs.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            const int st = check_launch("hsp plan upload");
+            hsp_free(p);
+            return st ? st : fail(GBSP_ERR_CUDA, "hsp plan upload");
+        }
+        int64_t blocks = ((int64_t)recs.size() + 255) / 256;
+        if (blocks > 32LL * sm_count()) blocks = 32LL * sm_count();
+        hsp_first_col_kernel<<<(unsigned)blocks, 256, 0, s>>>(p->d_recs, n_short, p->colidx);
+        count_launches(1);
+        int st = check_launch("hsp plan first columns");
+        if (st == GBSP_OK && cudaStreamSynchronize(s) != cudaSuccess) st = check_launch("hsp plan first columns");
+        if (st != GBSP_OK) {
+            hsp_free(p);
+            return st;
         }
     }
     *out = p;
@@ -291,8 +326,8 @@ GBSP_EXPORT int gbsp_hsp_plan_execute(const gbsp_hsp_plan *p, const gbsp_dense *
     P.dtype = GBSP_F32;
     HspLists L{};
     L.long_rows = p->d_rows;
-    L.short_rows = p->d_rows + p->n_long;
-    L.empty_rows = p->d_rows + p->n_long + p->n_short;
+    L.empty_rows = p->d_rows + p->n_long;
+    L.short_recs = p->d_recs;
     L.n_long = p->n_long;
     L.n_short = p->n_short;
     L.n_empty = p->n_empty;
