@@ -44,7 +44,7 @@ typedef enum {
     GBSP_ERR_INVALID_ARG = -1, /* null pointer, negative size, ld < cols, dtype mismatch */
     GBSP_ERR_INVALID_CSR = -2, /* validation found a malformed CSR */
     GBSP_ERR_ALIGN = -3,       /* a vectorised variant was forced on unaligned operands */
-    GBSP_ERR_UNSUPPORTED = -4, /* a combination this build does not implement */
+    GBSP_ERR_UNSUPPORTED = -4, /* a combination the library does not implement */
     GBSP_ERR_CUDA = -5,        /* a CUDA runtime call or launch failed */
     GBSP_ERR_OOM = -6,         /* library workspace could not be allocated */
     GBSP_ERR_TIMEOUT = -7      /* a bounded device-side wait gave up */
