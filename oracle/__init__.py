@@ -45,6 +45,7 @@ def _load():
         lib.oracle_e4m3_round.argtypes = [I64, P, P]
         lib.oracle_e4m3_decode.argtypes = [I64, P, P]
         lib.oracle_e4m3_rows.argtypes = [I64, P, I64, P, P, P]
+        lib.oracle_e4m3_fold.argtypes = [I64, I64, P, P, P, P, P, I, P, P, P, P]
         lib.oracle_max_threads.restype = I
         _lib = lib
     return _lib
@@ -143,6 +144,26 @@ def e4m3_rows_dequant(q, s, rowptr=None) -> np.ndarray:
         return v * np.asarray(s, dtype=np.float64)[:, None]
     lengths = np.diff(np.asarray(rowptr, dtype=np.int64))
     return v * np.repeat(np.asarray(s, dtype=np.float64), lengths)
+
+
+def e4m3_fold(rowptr, colidx, K, qa, sa, tb, threshold=0):
+    """Operands of the E4M3 condensed-tile SpMM: aligned 16 x 8 blocks with at least
+    ``threshold`` entries (10 when < 1) are dense; their entries take a~ = fl32(fl32(s_i
+    dec(q)) t_k), each row is requantised to E4M3 with the power-of-two scale u_i = 2^e (e
+    the smallest >= -126 with max |a~| <= 448 u_i).  Returns (codes, dense, eff, exps):
+    per entry the requantised code (the input code outside dense blocks), whether it is
+    dense, and the FP64 value the product uses (u_i dec(q') or s_i dec(q) t_k); per row e."""
+    lib = _load()
+    rp, ci = _c(rowptr, np.int32), _c(colidx, np.int32)
+    qa, sa, tb = _c(qa, np.uint8), _c(sa, np.float32), _c(tb, np.float32)
+    M, nnz = rp.shape[0] - 1, ci.shape[0]
+    codes = np.empty(nnz, np.uint8)
+    dense = np.empty(nnz, np.uint8)
+    eff = np.empty(nnz, np.float64)
+    exps = np.empty(M, np.int32)
+    lib.oracle_e4m3_fold(M, int(K), _p(rp), _p(ci), _p(qa), _p(sa), _p(tb), int(threshold), _p(codes), _p(dense),
+                         _p(eff), _p(exps))
+    return codes, dense.astype(bool), eff, exps
 
 
 def row_softmax(rowptr, E):

@@ -14,6 +14,7 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
@@ -193,4 +194,68 @@ void oracle_e4m3_rows(int64_t nrows, const int32_t *rowptr, int64_t ncols, const
             q[p] = e4m3_rne_sat(t);
         }
     }
+}
+
+/*
+ * Operands of the E4M3 condensed-tile SpMM (the library's reading of how per-row scales of
+ * B, which lie along the contraction of Eq. 1, reach tensor-core tiles; the paper itself
+ * has no tensor-core or FP8 design).  A is an M x K CSR matrix of E4M3 codes qa with row
+ * scales sa (value s_i * dec(q)); tb holds B's row scales t_k.
+ *   1. Blocks: A is cut into aligned blocks of 16 rows x 8 columns; a block whose stored
+ *      entries number at least `threshold` (10 when threshold < 1) is dense.
+ *   2. Fold: every entry of a dense block takes a~ = fl32(fl32(s_i * dec(q)) * t_k).
+ *   3. Row scale: for each row i, amax = max |a~| over the row's dense-block entries and
+ *      u_i = 2^e with e the smallest integer >= -126 such that amax <= 448 * 2^e.
+ *   4. Requantise: q'_ik = E4M3 (nearest, ties to even, saturating) of a~ / u_i.
+ *   5. The tensor cores then multiply u_i * dec(q'_ik); residual entries (outside dense
+ *      blocks) keep s_i * dec(q_ik) * t_k.
+ * Outputs per entry: codes (q' for dense entries, q otherwise), dense (1 / 0), eff (the
+ * FP64 value the product uses: u_i dec(q') or s_i dec(q) t_k, the latter exact in double);
+ * per row: exp_out (e; -126 for a row without dense entries).  Any output may be NULL.
+ */
+void oracle_e4m3_fold(int64_t M, int64_t K, const int32_t *rowptr, const int32_t *colidx,
+                      const uint8_t *qa, const float *sa, const float *tb, int threshold,
+                      uint8_t *codes, uint8_t *dense, double *eff, int32_t *exp_out) {
+    const int64_t bcols = (K + 7) / 8;
+    const int64_t nwin = (M + 15) / 16;
+    const int thr = threshold >= 1 ? threshold : 10;
+    /* step 1: stored entries per block, one window (16 rows) at a time */
+    int64_t *count = (int64_t *)calloc((size_t)(bcols > 0 ? bcols : 1), sizeof(int64_t));
+    for (int64_t w = 0; w < nwin; ++w) {
+        const int64_t r0 = 16 * w, r1 = r0 + 16 < M ? r0 + 16 : M;
+        for (int64_t b = 0; b < bcols; ++b) count[b] = 0;
+        for (int64_t i = r0; i < r1; ++i)
+            for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) count[colidx[p] / 8] += 1;
+        for (int64_t i = r0; i < r1; ++i) {
+            /* steps 2 and 3: fold the row's dense entries and find its exponent */
+            float amax = 0.0f;
+            for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+                const int is_dense = count[colidx[p] / 8] >= thr;
+                if (dense) dense[p] = (uint8_t)is_dense;
+                if (is_dense) {
+                    volatile float sq = sa[i] * (float)e4m3_value(qa[p]);
+                    volatile float at = sq * tb[colidx[p]];
+                    if (fabsf(at) > amax) amax = fabsf(at);
+                }
+            }
+            int e = -126;
+            while ((double)amax > ldexp(448.0, e)) ++e;
+            if (exp_out) exp_out[i] = e;
+            /* steps 4 and 5 */
+            for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+                const int is_dense = count[colidx[p] / 8] >= thr;
+                if (is_dense) {
+                    volatile float sq = sa[i] * (float)e4m3_value(qa[p]);
+                    volatile float at = sq * tb[colidx[p]];
+                    const uint8_t q2 = e4m3_rne_sat((float)ldexp((double)at, -e));
+                    if (codes) codes[p] = q2;
+                    if (eff) eff[p] = ldexp(e4m3_value(q2), e);
+                } else {
+                    if (codes) codes[p] = qa[p];
+                    if (eff) eff[p] = (double)sa[i] * e4m3_value(qa[p]) * (double)tb[colidx[p]];
+                }
+            }
+        }
+    }
+    free(count);
 }
