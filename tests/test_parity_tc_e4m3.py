@@ -3,9 +3,11 @@
 
 A holds codes q_ik with row scales s_i, B codes with row scales t_k; C = A B (Eq. 1) on the
 dequantised values.  The plan folds t into the dense-block values and requantises each
-window row with a power-of-two scale u_r; ``effective_values`` below restates that step on
-the CPU (FP32 products, E4M3 rounding of the oracle), so the expected result is the FP64
-oracle on exactly the operands the tensor cores multiply.  Integer inputs with unit scales
+window row with a power-of-two scale u_r; the oracle states that step (oracle.e4m3_fold,
+pinned by a hand-worked example in tests/test_oracle_fold.py), so the expected result is the
+FP64 oracle on exactly the operands the tensor cores multiply.  At the precision
+configuration the plan is also held to the E4M3 tolerance, 4e-2 of sum |a||b|, against the
+FP64 product of the original FP32 values.  Integer inputs with unit scales
 pass the requantisation unchanged and must match the oracle bit for bit.
 """
 import numpy as np
@@ -28,30 +30,9 @@ def gb():
 
 
 def effective_values(rowptr, colidx, K, qa, sa, tb, threshold):
-    """Per stored entry, the FP64 value the plan multiplies with decode(qb).
-
-    Entries of dense blocks (16 x 8, aligned, >= threshold entries): u_r decode(e4m3(a~ / u_r))
-    with a~ = fl32(fl32(s_i decode(q)) t_k) and u_r = 2^e, e the smallest exponent (>= -126)
-    with max |a~| <= 448 u_r over the row's dense-block entries.  Residual entries:
-    s_i decode(q) t_k."""
-    rp = np.asarray(rowptr, np.int64)
-    ci = np.asarray(colidx, np.int64)
-    M = rp.size - 1
-    rows = np.repeat(np.arange(M), np.diff(rp))
-    deq = oracle.e4m3_decode(qa)
-    s32, t32 = np.asarray(sa, np.float32), np.asarray(tb, np.float32)
-    eff = s32[rows].astype(np.float64) * deq * t32[ci].astype(np.float64)
-    key = (rows // 16) * ((K + 7) // 8) + ci // 8
-    _, inv, cnt = np.unique(key, return_inverse=True, return_counts=True)
-    dense = cnt[inv] >= (threshold if threshold >= 1 else 10)  # the E4M3 default
-    at = (s32[rows] * deq.astype(np.float32)).astype(np.float32) * t32[ci]
-    amax = np.zeros(M, np.float32)
-    np.maximum.at(amax, rows[dense], np.abs(at[dense]))
-    m, E = np.frexp(amax)
-    e = np.where(amax > 0, np.maximum(np.where(m <= 0.875, E - 9, E - 8), -126), 0).astype(np.int64)
-    ed = e[rows[dense]]
-    scaled = (at[dense].astype(np.float64) * np.ldexp(1.0, -ed)).astype(np.float32)
-    eff[dense] = oracle.e4m3_decode(oracle.e4m3_round(scaled)) * np.ldexp(1.0, ed)
+    """Per stored entry, the FP64 value the plan multiplies with decode(qb), and whether the
+    entry lies in a dense block: the oracle's statement of the fold (oracle.e4m3_fold)."""
+    _, dense, eff, _ = oracle.e4m3_fold(rowptr, colidx, K, qa, sa, tb, threshold)
     return eff, dense
 
 
