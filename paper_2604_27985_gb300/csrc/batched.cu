@@ -304,10 +304,15 @@ int create(int kind, int G, const gbsp_csr *A, const gbsp_dense *B, gbsp_dense *
         batch_free(p);
         return fail(GBSP_ERR_OOM, "batch plan: allocation failed");
     }
-    if ((nsp && cudaMemcpy(p->d_spmm, sp.data(), sizeof(SpmmProblem) * nsp, cudaMemcpyHostToDevice) != cudaSuccess) ||
-        (nsd && cudaMemcpy(p->d_sddmm, sd.data(), sizeof(SddmmProblem) * nsd, cudaMemcpyHostToDevice) != cudaSuccess) ||
-        (!tiles.empty() &&
-         cudaMemcpy(p->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice) != cudaSuccess)) {
+    // stream-ordered uploads, complete before the host vectors go out of scope and before
+    // the graph that reads them is recorded or replayed
+    if ((nsp && cudaMemcpyAsync(p->d_spmm, sp.data(), sizeof(SpmmProblem) * nsp, cudaMemcpyHostToDevice, s) !=
+                    cudaSuccess) ||
+        (nsd && cudaMemcpyAsync(p->d_sddmm, sd.data(), sizeof(SddmmProblem) * nsd, cudaMemcpyHostToDevice, s) !=
+                    cudaSuccess) ||
+        (!tiles.empty() && cudaMemcpyAsync(p->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(),
+                                           cudaMemcpyHostToDevice, s) != cudaSuccess) ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
         int st = check_launch("batch plan upload");
         batch_free(p);
         return st ? st : fail(GBSP_ERR_CUDA, "batch plan upload");

@@ -407,10 +407,13 @@ GBSP_EXPORT int gbsp_gnn_plan_create_ex(int G, const gbsp_csr *S, const gbsp_den
         gnn_free(p);
         return fail(GBSP_ERR_OOM, "gnn plan: allocation failed");
     }
-    if ((G > 0 && cudaMemcpy(p->d_graphs, graphs.data(), sizeof(GraphDesc) * G, cudaMemcpyHostToDevice) !=
+    // stream-ordered uploads, complete before the host vectors go out of scope and before
+    // the graph that reads them is recorded or replayed
+    if ((G > 0 && cudaMemcpyAsync(p->d_graphs, graphs.data(), sizeof(GraphDesc) * G, cudaMemcpyHostToDevice, s) !=
                       cudaSuccess) ||
-        (!tiles.empty() &&
-         cudaMemcpy(p->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice) != cudaSuccess)) {
+        (!tiles.empty() && cudaMemcpyAsync(p->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(),
+                                           cudaMemcpyHostToDevice, s) != cudaSuccess) ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
         st = check_launch("gnn plan upload");
         gnn_free(p);
         return st ? st : fail(GBSP_ERR_CUDA, "gnn plan upload");

@@ -261,7 +261,9 @@ GBSP_EXPORT int gbsp_hsp_plan_create(const gbsp_csr *A, void *stream, gbsp_hsp_p
             hsp_free(p);
             return fail(GBSP_ERR_OOM, "hsp plan: allocation failed");
         }
-        if (cudaMemcpy(p->d_rows, rows.data(), sizeof(int32_t) * rows.size(), cudaMemcpyHostToDevice) !=
+        // stream-ordered upload: a pageable cudaMemcpy neither orders against a non-blocking
+        // stream nor guarantees that the DMA has landed when it returns
+        if (cudaMemcpyAsync(p->d_rows, rows.data(), sizeof(int32_t) * rows.size(), cudaMemcpyHostToDevice, s) !=
             cudaSuccess) {
             const int st = check_launch("hsp plan upload");
             hsp_free(p);
@@ -274,7 +276,8 @@ GBSP_EXPORT int gbsp_hsp_plan_create(const gbsp_csr *A, void *stream, gbsp_hsp_p
             hsp_free(p);
             return fail(GBSP_ERR_OOM, "hsp plan: allocation failed");
         }
-        if (cudaMemcpy(p->d_recs, recs.data(), sizeof(int4) * recs.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        if (cudaMemcpyAsync(p->d_recs, recs.data(), sizeof(int4) * recs.size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess) {
             const int st = check_launch("hsp plan upload");
             hsp_free(p);
             return st ? st : fail(GBSP_ERR_CUDA, "hsp plan upload");
@@ -283,12 +286,18 @@ GBSP_EXPORT int gbsp_hsp_plan_create(const gbsp_csr *A, void *stream, gbsp_hsp_p
         if (blocks > 32LL * sm_count()) blocks = 32LL * sm_count();
         hsp_first_col_kernel<<<(unsigned)blocks, 256, 0, s>>>(p->d_recs, n_short, p->colidx);
         count_launches(1);
-        int st = check_launch("hsp plan first columns");
-        if (st == GBSP_OK && cudaStreamSynchronize(s) != cudaSuccess) st = check_launch("hsp plan first columns");
+        const int st = check_launch("hsp plan first columns");
         if (st != GBSP_OK) {
+            cudaStreamSynchronize(s);
             hsp_free(p);
             return st;
         }
+    }
+    // the uploads read rows and recs, which go out of scope on return
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        const int st = check_launch("hsp plan upload");
+        hsp_free(p);
+        return st ? st : fail(GBSP_ERR_CUDA, "hsp plan upload");
     }
     *out = p;
     return ok();

@@ -127,3 +127,23 @@ def test_hsp_argument_errors(gb):
         plan.execute(torch.zeros((A.K, 6), device="cuda"))
     with pytest.raises(gb.GbspError, match="INVALID_ARG"):
         plan.execute(torch.zeros((A.K - 1, 8), device="cuda"))
+
+
+def test_hsp_plan_created_on_nonblocking_stream(gb):
+    """Plan creation uploads its row lists and records on the caller's stream; on a
+    non-blocking side stream (which does not order against the legacy default stream) the
+    first execution on that stream must still see every record."""
+    import torch
+
+    A = gen.csr_from_lengths(mixed_lengths(20000, 481), 3000, seed=482)
+    vals = gen.vals_int(A.nnz, 483)
+    B = gen.dense_int(A.K, 64, 484)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        rp, ci, v, Bd = dev(A.rowptr), dev(A.colidx), dev(vals), dev(B)
+        plan = gb.HspPlan(rp, ci, v, A.K, stream=side)
+        C = plan.execute(Bd, stream=side)
+    side.synchronize()
+    want, _ = oracle.spmm(A.rowptr, A.colidx, vals, B)
+    assert np.array_equal(C.cpu().numpy().astype(np.float64), want)
+    plan.close()
