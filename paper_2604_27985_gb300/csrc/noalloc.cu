@@ -3,10 +3,9 @@
 //
 // Who needs it: a caller whose device memory is entirely handed out by another allocator
 // (a framework's caching allocator that reserved nearly all of HBM, a fixed arena in a
-// serving process) can see a driver allocation fail at call time; a latency-bound loop
-// cannot afford an allocation that may synchronise; and code built into a captured CUDA
-// graph must not leave allocation nodes in it.  The general entry points take their
-// merge-path carry buffers from a library-owned pool, which none of these callers can
+// serving process) can see a driver allocation fail at call time, and a latency-bound
+// loop cannot afford an allocation that may synchronise.  The general entry points take
+// their merge-path carry buffers from a library-owned pool, which neither caller can
 // accept; this one takes them from a file-scope device array instead.
 #include <mutex>
 
@@ -27,8 +26,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 std::mutex g_mu;
 void *g_scratch_addr[64] = {nullptr};
 
-// Device address of the scratch array on the current device, looked up once per device.
-// The host-side name of the array is only a stand-in, never a device address.
+// Device address of the scratch array on the current device, looked up once per device
+// and kept for the life of the process (a cudaDeviceReset makes it stale; the header says
+// so).  The host-side name of the array is only a stand-in, never a device address.
 int scratch_address(void **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
