@@ -245,6 +245,31 @@ def _gather_ceiling(p, nnz, kernel_ms):
             "probe_gbs": p["gbs"], "kernel_gbs": round(achieved, 1), "frac": round(achieved / p["gbs"], 4)}
 
 
+def l2_roofline(kernel, nnz, row_bytes, probe_gbs, ms, hbm_peak, hbm_kind, compulsory, gather_model, traffic):
+    """Roofline of a gather kernel whose gathered operand sits in L2: the binding roof is
+    the L2 -> SM gather path, measured in the same run by the gather probe over the
+    workload's own column indices and rows of the same size.  achieved = the gathered-row
+    bytes of one launch (nnz * row_bytes) / its event-timed duration; frac = achieved /
+    probe.  Beside it: the HBM fraction on compulsory bytes (every operand moved once)
+    against the measured copy peak, and the gather-model bytes (which count L2 hits and so
+    exceed HBM) for reference."""
+    achieved = nnz * row_bytes / (ms / 1e3) / 1e9
+    return {"bound": "l2", "kernel": kernel, "achieved": round(achieved, 1), "peak": probe_gbs,
+            "peak_kind": f"measured in this run: gather probe, {row_bytes}-byte rows over the workload's colidx",
+            "unit": "GB/s", "frac": round(achieved / probe_gbs, 4), "traffic": traffic,
+            "algorithmic_bytes_per_launch": int(nnz * row_bytes), "ms_per_launch": round(ms, 4),
+            "hbm": {"bytes": int(compulsory), "achieved": round(compulsory / (ms / 1e3) / 1e9, 1), "peak": hbm_peak,
+                    "peak_kind": hbm_kind, "frac": round(compulsory / (ms / 1e3) / 1e9 / hbm_peak, 4),
+                    "model": "compulsory: every operand once"},
+            "gather_model_bytes": int(gather_model),
+            "gather_model_gbs": round(gather_model / (ms / 1e3) / 1e9, 1)}
+
+
+def compulsory_bytes_sddmm(nnz, m, n, kd, v=4, e=4):
+    """Every operand of one SDDMM moved once: row pointers, indices, values, X, Y, out."""
+    return 4 * (m + 1) + (4 + v + 4) * nnz + (m + n) * kd * e
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -335,8 +360,6 @@ def run_ours(args):
     peak, peak_kind = peaks()
     spmm_bytes = gather_bytes_spmm(nnz, M, N_SPMM)
     sddmm_bytes = gather_bytes_sddmm(nnz, M, KD_SDDMM)
-    spmm_gbs = spmm_bytes / (spmm_ms / 1e3) / 1e9
-    sddmm_gbs = sddmm_bytes / (sddmm_ms / 1e3) / 1e9
     traffic_spmm, traffic_sddmm = kernel_traffic()
     comp = compulsory_bytes_spmm(nnz, M, K, N_SPMM)
 
@@ -349,7 +372,7 @@ def run_ours(args):
         model = sel.Selector.load()
         v_idx = model.choose(rp, ci, K, N_SPMM, 0)
         kw = gb.variant_options(v_idx)
-        ms_sel = _event_ms(lambda: gb.spmm(rp, ci, v, Bd, out=C, stream=stream, **kw), 50, 5, stream)
+        ms_sel = _event_ms(lambda: model.run_spmm(v_idx, rp, ci, v, Bd, C, stream=stream), 50, 5, stream)
         qa, qB, qX, qY = (gb.quantize_bf16(a) for a in (v, Bd, Xd, Yd))
         ms_bs = _event_ms(lambda: gb.spmm(rp, ci, qa, qB, out=C, stream=stream), 50, 5, stream)
         ms_bd = _event_ms(lambda: gb.sddmm(rp, ci, v, qX, qY, out=out, stream=stream), 50, 5, stream)
@@ -388,18 +411,11 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "nnz": nnz, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2 (CSR arrays 344 MB per step), no flush",
                    "variant": "auto (rowsplit SpMM, rowsplit SDDMM)"},
-        "roofline": {"bound": "hbm", "kernel": "spmm (Eq. 1), gather model",
-                     "achieved": round(spmm_gbs, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": round(spmm_gbs / peak, 4), "traffic": traffic_spmm,
-                     "algorithmic_bytes_per_launch": spmm_bytes, "ms_per_launch": round(spmm_ms, 4),
-                     "gather_ceiling": _gather_ceiling(probe["spmm"], nnz, spmm_ms)},
-        "roofline_sddmm": {"bound": "hbm", "kernel": "sddmm (Eq. 2), gather model",
-                           "achieved": round(sddmm_gbs, 1), "peak": peak, "unit": "GB/s",
-                           "frac": round(sddmm_gbs / peak, 4), "traffic": traffic_sddmm,
-                           "algorithmic_bytes_per_launch": sddmm_bytes, "ms_per_launch": round(sddmm_ms, 4),
-                           "gather_ceiling": _gather_ceiling(probe["sddmm"], nnz, sddmm_ms)},
-        "roofline_compulsory_spmm": {"bytes": comp, "achieved": round(comp / (spmm_ms / 1e3) / 1e9, 1),
-                                     "frac": round(comp / (spmm_ms / 1e3) / 1e9 / peak, 4)},
+        "roofline": l2_roofline("spmm (Eq. 1), row split", nnz, N_SPMM * 4, probe["spmm"]["gbs"], spmm_ms, peak,
+                                peak_kind, comp, spmm_bytes, traffic_spmm),
+        "roofline_sddmm": l2_roofline("sddmm (Eq. 2), row split", nnz, KD_SDDMM * 4, probe["sddmm"]["gbs"], sddmm_ms,
+                                      peak, peak_kind, compulsory_bytes_sddmm(nnz, M, K, KD_SDDMM), sddmm_bytes,
+                                      traffic_sddmm),
         "spmm_gflops": round(2.0 * nnz * N_SPMM / (spmm_ms / 1e3) / 1e9, 1),
         "sddmm_gflops": round(2.0 * nnz * KD_SDDMM / (sddmm_ms / 1e3) / 1e9, 1),
         "e2e": {"value": round(world * gflop / (e2e_ms / 1e3), 2), "unit": "GFLOP/s", "ms_per_step": round(e2e_ms, 4),
@@ -443,26 +459,48 @@ def _line(metric, value, unit, ms, args, dtype, config, **extra):
     print(json.dumps(out), flush=True)
 
 
+def _probe_gbs(gb, table, ci, row_bytes, stream):
+    """GB/s of the gather probe over these column indices and rows of row_bytes bytes (the
+    better of 4 and 8 rows in flight per lane)."""
+    ms = min(_event_ms(lambda: gb.gather_probe(table, ci, row_bytes, unroll=u, stream=stream), 20, 3, stream)
+             for u in (4, 8))
+    return round(ci.numel() * row_bytes / (ms / 1e3) / 1e9, 1)
+
+
+def _errors(gpu, ref, scale):
+    """max and mean of |gpu - ref| / scale over the outputs with scale > 0."""
+    gpu = np.asarray(gpu, dtype=np.float64)
+    nz = scale > 0
+    rel = np.abs(gpu[nz] - ref[nz]) / scale[nz]
+    return {"max": float(rel.max()) if rel.size else 0.0, "mean": float(rel.mean()) if rel.size else 0.0}
+
+
 def run_precision(args):
     """16,384^2 at 90%, N = Kd = 256: SpMM + SDDMM in FP32, BF16, E4M3 (CUDA cores) and the
     BF16 / E4M3 condensed-tile tensor-core plans (SpMM and SDDMM), on the uniform and the
-    clustered layouts."""
+    clustered layouts.  Per form: event-timed SpMM and SDDMM, the L2 roof (gathered-row
+    bytes per second against the gather probe over the same indices and row size), the HBM
+    fraction on compulsory bytes, and, outside the timed region, the max and mean of
+    |err| / sum |a||b| against the FP64 oracle on the ORIGINAL FP32 values over 400
+    sampled rows (quantisation included)."""
     import torch
 
+    import oracle
     import paper_2604_27985_gb300 as gb
 
     dev = torch.device("cuda")
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     stream = torch.cuda.current_stream()
-    peak, _ = peaks()
-    forms = {}
+    peak, peak_kind = peaks()
+    forms, launches = {}, 0
+    W = 256
     for layout in args.precision_layouts.split(","):
         A = (gen.csr_uniform(16384, 16384, 0.9, seed=2001) if layout == "uniform"
              else gen.csr_clustered(16384, 16384, 0.9, seed=2002))
-        B, X, Y = (gen.dense_normal(16384, 256, 2003 + k) for k in range(3))
+        B, X, Y = (gen.dense_normal(16384, W, 2003 + k) for k in range(3))
         rp, ci, v = t(A.rowptr), t(A.colidx), t(A.vals)
         Bd, Xd, Yd = t(B), t(X), t(Y)
-        C = torch.empty((A.M, 256), device=dev)
+        C = torch.empty((A.M, W), device=dev)
         out = torch.empty(A.nnz, device=dev)
         qa, qb, qx, qy = gb.quantize_bf16(v), gb.quantize_bf16(Bd), gb.quantize_bf16(Xd), gb.quantize_bf16(Yd)
         ea, sa = gb.quantize_e4m3_rows(v, rp)
@@ -472,6 +510,16 @@ def run_precision(args):
         plan = gb.TcPlan(rp, ci, qa, A.K)
         plan8 = gb.TcPlan(rp, ci, ea, A.K, row_scale=sa)
         info, info8 = plan.info(), plan8.info()
+        # sampled rows and the oracle on the original FP32 values (outside any timed region)
+        wins = np.sort(np.random.default_rng(17).choice(A.M // 16, 25, replace=False))
+        rows = (wins[:, None] * 16 + np.arange(16)).ravel()
+        lens = np.diff(A.rowptr.astype(np.int64))[rows]
+        idx = np.concatenate([np.arange(A.rowptr[r], A.rowptr[r + 1]) for r in rows])
+        srp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+        ref_c, sc_c = oracle.spmm(srp, A.colidx[idx], A.vals[idx], B)
+        ref_o, sc_o = oracle.sddmm(srp, A.colidx[idx], A.vals[idx], X[rows], Y)
+        probes = {rb: _probe_gbs(gb, tb_, ci, rb, stream)
+                  for rb, tb_ in ((W * 4, Bd), (W * 2, qb), (W, eb))}
         runs = {
             "fp32": (lambda: gb.spmm(rp, ci, v, Bd, out=C), lambda: gb.sddmm(rp, ci, v, Xd, Yd, out=out), 4, 4),
             "bf16": (lambda: gb.spmm(rp, ci, qa, qb, out=C), lambda: gb.sddmm(rp, ci, v, qx, qy, out=out), 2, 2),
@@ -481,16 +529,32 @@ def run_precision(args):
             "tc_e4m3": (lambda: plan8.execute(eb, out=C, row_scale=sb),
                         lambda: plan8.sddmm(v, ex, ey, out=out, x_scale=ux, y_scale=uy), 1, 1),
         }
-        for name, (f_spmm, f_sddmm, vb, eb_) in runs.items():
+        for name, (f_spmm, f_sddmm, vb, e_) in runs.items():
+            l0 = gb.launch_count()
             ms_a = _event_ms(f_spmm, args.steps, args.warmup, stream)
+            launches += gb.launch_count() - l0
+            err_c = _errors(C.cpu().numpy()[rows], ref_c, sc_c)
+            l0 = gb.launch_count()
             ms_b = _event_ms(f_sddmm, args.steps, args.warmup, stream)
-            gbytes = (A.nnz * (4 + vb + 256 * eb_) + A.M * (4 + 4 * 256)) / 1e9
+            launches += gb.launch_count() - l0
+            err_o = _errors(out.cpu().numpy()[idx], ref_o, sc_o)
+            rb = W * e_
+            pinfo = info if name == "tc_bf16" else info8 if name == "tc_e4m3" else None
+            # gathered B rows: one per stored entry on the CSR kernels; a plan gathers 8 per
+            # dense block (each once) and one per residual entry
+            rows_gathered = (A.nnz if pinfo is None else pinfo["residual_nnz"] + 8 * pinfo["dense_blocks"])
+            comp_a = compulsory_bytes_spmm(A.nnz, A.M, A.K, W, v=vb, e=e_)
+            comp_b = compulsory_bytes_sddmm(A.nnz, A.M, A.K, W, v=4, e=e_)
             forms[f"{layout}/{name}"] = {
                 "spmm_ms": round(ms_a, 4), "sddmm_ms": round(ms_b, 4),
-                "spmm_gflops": round(2 * A.nnz * 256 / ms_a / 1e6, 1),
-                "sddmm_gflops": round(2 * A.nnz * 256 / ms_b / 1e6, 1),
-                "step_gflops": round(4 * A.nnz * 256 / (ms_a + ms_b) / 1e6, 1),
-                "spmm_gather_frac": round(gbytes / (ms_a / 1e3) / peak, 3)}
+                "spmm_gflops": round(2 * A.nnz * W / ms_a / 1e6, 1),
+                "sddmm_gflops": round(2 * A.nnz * W / ms_b / 1e6, 1),
+                "step_gflops": round(4 * A.nnz * W / (ms_a + ms_b) / 1e6, 1),
+                "spmm_l2": {"gathered_gbs": round(rows_gathered * rb / ms_a / 1e6, 1), "probe_gbs": probes[rb],
+                            "frac": round(rows_gathered * rb / ms_a / 1e6 / probes[rb], 4)},
+                "spmm_hbm_frac": round(comp_a / ms_a / 1e6 / peak, 4),
+                "sddmm_hbm_frac": round(comp_b / ms_b / 1e6 / peak, 4),
+                "err_vs_fp64_of_fp32_inputs": {"spmm": err_c, "sddmm": err_o}}
         forms[f"{layout}/tc_plan"] = info
         forms[f"{layout}/tc_plan_e4m3"] = info8
         for p_ in (plan, plan8):
@@ -503,7 +567,10 @@ def run_precision(args):
           "GFLOP/s", forms[best]["spmm_ms"] + forms[best]["sddmm_ms"], args, best.split("/")[1],
           {"workload": "CSR 16384x16384 at 90% (uniform seed 2001, clustered 16x8 blocks at 40% fill seed 2002), "
                        "SpMM N=256 + SDDMM Kd=256", "best_form": best,
-           f"fp32_{last}_step_ms": round(base, 4)}, forms=forms)
+           f"fp32_{last}_step_ms": round(base, 4),
+           "errors": "max / mean of |err| / sum|a||b| against FP64 of the original FP32 values, 400 sampled rows",
+           "tolerances": {"fp32": 1e-5, "bf16": 1e-2, "e4m3": 4e-2}, "hbm_peak": peak, "hbm_peak_kind": peak_kind},
+          forms=forms, gpu_launches=int(launches))
 
 
 def run_gnn(args):
@@ -530,16 +597,40 @@ def run_gnn(args):
     launches0 = gb.launch_count()
     ms = _event_ms(plan.execute, args.steps, args.warmup, stream)
     launches = (gb.launch_count() - launches0) // (args.steps + args.warmup)
-    peak, _ = peaks()
+    peak, peak_kind = peaks()
     info = plan.info()
+    # L2 roof: each graph's H (at most 50,000 x 256 BF16 = 25.6 MB) sits in L2 while its
+    # tiles run, so the H_j gathers (2N bytes per edge) are held against the gather probe
+    # over each width class's own indices on a 50,000-row table of that row size.
+    edges_by_w, idx_by_w = {}, {}
+    for (A, N) in graphs:
+        edges_by_w[N] = edges_by_w.get(N, 0) + A.nnz
+        idx_by_w.setdefault(N, []).append(A.colidx)
+    t_ceiling, gathered = 0.0, 0.0
+    probe = {}
+    for N, parts in sorted(idx_by_w.items()):
+        ci = torch.from_numpy(np.concatenate(parts)).to(dev)
+        table = torch.zeros((50000, N), dtype=torch.bfloat16, device=dev)
+        probe[N] = _probe_gbs(gb, table, ci, 2 * N, stream)
+        t_ceiling += edges_by_w[N] * 2 * N / (probe[N] * 1e9)
+        gathered += edges_by_w[N] * 2 * N
+        del ci, table
+    comp = sum(A.nnz * 12 + A.M * (4 + 4 * N) for A, N in graphs)
     chain = "SDDMM->row softmax->SpMM" if args.gat else "SDDMM->SpMM"
     _line(f"batched {chain} GFLOP/s (4*nnz*N over the batch)", flop / ms / 1e6, "GFLOP/s", ms, args, "bf16",
           {"workload": f"{len(graphs)} of the 512 graphs (nodes log-uniform [1000, 50000], power-law degree "
                        "(mean 16, max 2048), row-normalised values, BF16 features N in {64,128,256}, seed 3000)",
            "softmax": bool(args.gat), **info},
-          roofline={"bound": "hbm", "kernel": "gnn_kernel, gather model", "achieved": round(gbytes / ms * 1e3, 1),
-                    "peak": peak, "unit": "GB/s", "frac": round(gbytes / ms * 1e3 / peak, 4),
-                    "algorithmic_bytes_per_launch": int(gbytes * 1e9)},
+          roofline={"bound": "l2", "kernel": "gnn_kernel: H_j gathered once per edge (2N bytes)",
+                    "achieved": round(gathered / ms / 1e6, 1), "unit": "GB/s",
+                    "peak": round(gathered / t_ceiling / 1e9, 1),
+                    "peak_kind": "measured in this run: gather probe per width class over the batch's own indices",
+                    "probe_gbs_by_width": probe, "frac": round(t_ceiling * 1e3 / ms, 4),
+                    "algorithmic_bytes_per_launch": int(gathered),
+                    "hbm": {"bytes": int(comp), "achieved": round(comp / ms / 1e6, 1), "peak": peak,
+                            "peak_kind": peak_kind, "frac": round(comp / ms / 1e6 / peak, 4),
+                            "model": "compulsory: indices, values, E, H and O once"},
+                    "gather_model_bytes": int(gbytes * 1e9)},
           gpu_launches_per_step=int(launches))
 
 
@@ -569,8 +660,12 @@ def run_sweep(args):
     for n, sp, layout, seed in mats:
         A = (gen.csr_uniform if layout == "uniform" else gen.csr_powerlaw)(n, n, sp, seed=seed)
         rp, ci, v = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.colidx, A.vals))
+        touched = int(np.unique(A.colidx).size)  # B (or Y) rows read at least once
         g = torch.Generator(device=dev)
         g.manual_seed(seed)
+        probe = {}
+        sells = {"sell_c64_sigma_all": gb.SellPlan(rp, ci, v, n, C=64, sigma=0),
+                 "sell_c64_sigma4096": gb.SellPlan(rp, ci, v, n, C=64, sigma=4096)}
         for op, widths in (("spmm", (32, 64, 128)), ("sddmm", (32, 128))):
             for w in widths:
                 if op == "spmm":
@@ -590,20 +685,42 @@ def run_sweep(args):
                 f = 2.0 * A.nnz * w
                 flop_sum += f
                 ms_sum += ms
+                if w not in probe:
+                    probe[w] = _probe_gbs(gb, Bd if op == "spmm" else Yd, ci, 4 * w, stream)
+                comp = (compulsory_bytes_spmm(A.nnz, n, touched, w) if op == "spmm"
+                        else compulsory_bytes_sddmm(A.nnz, n, touched, w))
                 pt = {"n": n, "sparsity": sp, "rows": layout, "op": op, "width": w, "nnz": A.nnz,
                       "ms": round(ms, 4), "gflops": round(f / ms / 1e6, 1),
-                      "gather_gbs": round(nbytes / ms / 1e6, 1), "frac": round(nbytes / ms / 1e6 / peak, 4)}
-                if op == "spmm":  # the shipped selector's variant for this matrix and width (untimed choice)
+                      "gathered_gbs": round(A.nnz * 4 * w / ms / 1e6, 1), "probe_gbs": probe[w],
+                      "frac": round(A.nnz * 4 * w / ms / 1e6 / probe[w], 4),
+                      "hbm_frac": round(comp / ms / 1e6 / peak, 4), "gather_model_gbs": round(nbytes / ms / 1e6, 1)}
+                # every explicit split beside the automatic one (untimed choice, timed runs)
+                splits = ("rowsplit", "merge", "rowgroup") if op == "spmm" else ("rowsplit", "merge", "entry")
+                for sp_name in splits:
+                    if op == "spmm":
+                        f_sp = lambda: gb.spmm(rp, ci, v, Bd, out=C, stream=stream, variant=sp_name)
+                    else:
+                        f_sp = lambda: gb.sddmm(rp, ci, v, Xd, Yd, out=out, stream=stream, variant=sp_name)
+                    pt[f"{sp_name}_ms"] = round(_event_ms(f_sp, args.steps, args.warmup, stream), 4)
+                best = min(pt[f"{x}_ms"] for x in splits)
+                pt["auto_vs_best_split"] = round(ms / best - 1, 4)
+                pt["auto_variant"] = gb.auto_choice(rp, n, ci, op=op, b_bytes=4 * w * n, row_bytes=4 * w)[0]
+                if op == "spmm":
+                    # SELL-C-sigma (plans built once per matrix, outside the timed calls)
+                    for key_, sell_ in sells.items():
+                        pt[f"{key_}_ms"] = round(_event_ms(lambda: sell_.execute(Bd, out=C, stream=stream),
+                                                           args.steps, args.warmup, stream), 4)
+                    # the shipped selector's variant for this matrix and width (untimed choice)
                     v_idx = model.choose(rp, ci, n, w, 0)
                     kw = gb.variant_options(v_idx)
-                    ms_sel = _event_ms(lambda: gb.spmm(rp, ci, v, Bd, out=C, stream=stream, **kw), args.steps,
+                    ms_sel = _event_ms(lambda: model.run_spmm(v_idx, rp, ci, v, Bd, C, stream=stream), args.steps,
                                        args.warmup, stream)
-                    ms_mp = _event_ms(lambda: gb.spmm(rp, ci, v, Bd, out=C, stream=stream, variant="merge"),
-                                      args.steps, args.warmup, stream)
                     pt.update(selector_variant=v_idx, selector_options=kw, selector_ms=round(ms_sel, 4),
-                              selector_frac=round(nbytes / ms_sel / 1e6 / peak, 4), merge_ms=round(ms_mp, 4))
+                              selector_frac=round(A.nnz * 4 * w / ms_sel / 1e6 / probe[w], 4))
                 points.append(pt)
                 del fn
+        for sell_ in sells.values():
+            sell_.close()
         del A, rp, ci, v
         torch.cuda.empty_cache()
     _line("SpMM & SDDMM GFLOP/s (2*nnz*N) over the plain-FP32 scale/sparsity sweep", flop_sum / ms_sum / 1e6,
@@ -612,9 +729,14 @@ def run_sweep(args):
                        + ", uniform and power-law rows (Zipf 1.5, cap 4096), values U[-1,1]; SpMM N 32/64/128, "
                        "SDDMM Kd 32/128, dense operands N(0,1); automatic variant; CSR arrays larger than L2",
            "points": points},
-          roofline={"bound": "hbm", "kernel": "spmm / sddmm, gather model", "peak": peak, "peak_kind": peak_kind,
+          roofline={"bound": "l2", "kernel": "spmm / sddmm: gathered rows against the gather probe over each "
+                                        "matrix's own indices and row size (measured in this run)",
                     "unit": "GB/s", "frac_min": min(p["frac"] for p in points),
-                    "frac_max": max(p["frac"] for p in points)},
+                    "frac_max": max(p["frac"] for p in points),
+                    "hbm": {"peak": peak, "peak_kind": peak_kind, "model": "compulsory: every operand once "
+                            "(rows of B / Y that are read at least once)",
+                            "frac_min": min(p["hbm_frac"] for p in points),
+                            "frac_max": max(p["hbm_frac"] for p in points)}},
           gpu_launches=int(launches))
 
 
@@ -638,14 +760,16 @@ def run_kbin(args):
         rp, ci, v = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.colidx, A.vals))
         g = torch.Generator(device=dev)
         g.manual_seed(seed)
+        touched = int(np.unique(A.colidx).size)
         for N in (32, 64, 128):
             Bd = torch.randn((n, N), generator=g, device=dev)
             C = torch.empty((n, N), device=dev)
             f = 2.0 * A.nnz * N
             nbytes = gather_bytes_spmm(A.nnz, n, N)
+            pgbs = _probe_gbs(gb, Bd, ci, 4 * N, stream)
             pt = {"rows": layout, "N": N, "nnz": A.nnz,
-                  "rowsplit_ms": round(_event_ms(lambda: gb.spmm(rp, ci, v, Bd, out=C, stream=stream), args.steps,
-                                                 args.warmup, stream), 4),
+                  "rowsplit_ms": round(_event_ms(lambda: gb.spmm(rp, ci, v, Bd, out=C, variant="rowsplit",
+                                                                 stream=stream), args.steps, args.warmup, stream), 4),
                   "merge_ms": round(_event_ms(lambda: gb.spmm(rp, ci, v, Bd, out=C, variant="merge", stream=stream),
                                               args.steps, args.warmup, stream), 4)}
             for mb in (24, 48, 96):
@@ -656,8 +780,11 @@ def run_kbin(args):
                     launches += gb.launch_count() - l0
                     flop_sum += f
                     ms_sum += ms
+                    comp = compulsory_bytes_spmm(A.nnz, n, touched, N)
                     pt.update(kbin_ms=round(ms, 4), slices=plan.info()["slices"], gflops=round(f / ms / 1e6, 1),
-                              gather_gbs=round(nbytes / ms / 1e6, 1), frac=round(nbytes / ms / 1e6 / peak, 4),
+                              gathered_gbs=round(A.nnz * 4 * N / ms / 1e6, 1), probe_gbs=pgbs,
+                              frac=round(A.nnz * 4 * N / ms / 1e6 / pgbs, 4),
+                              hbm_frac=round(comp / ms / 1e6 / peak, 4), gather_model_gbs=round(nbytes / ms / 1e6, 1),
                               c_partial_bytes=int((2 * plan.info()["slices"] - 1) * n * N * 4))
                 pt[f"kbin_{mb}mb_ms"] = round(ms, 4)
                 plan.close()
@@ -670,9 +797,12 @@ def run_kbin(args):
           {"workload": "1048576^2 at 99.99% (109,951,163 nonzeros), uniform and power-law rows, values U[-1,1]; "
                        "B N(0,1) FP32 with N 32/64/128; default 48 MB B slices; CSR larger than L2",
            "points": points},
-          roofline={"bound": "hbm", "kernel": "kbin_pass_kernel, gather model", "peak": peak,
-                    "peak_kind": peak_kind, "unit": "GB/s", "frac_min": min(p["frac"] for p in points),
-                    "frac_max": max(p["frac"] for p in points)},
+          roofline={"bound": "l2", "kernel": "kbin_pass_kernel: gathered B rows against the gather probe over "
+                                        "the same indices and row size (measured in this run)", "unit": "GB/s",
+                    "frac_min": min(p["frac"] for p in points), "frac_max": max(p["frac"] for p in points),
+                    "hbm": {"peak": peak, "peak_kind": peak_kind, "model": "compulsory: every operand once",
+                            "frac_min": min(p["hbm_frac"] for p in points),
+                            "frac_max": max(p["hbm_frac"] for p in points)}},
           gpu_launches=int(launches))
 
 
@@ -718,6 +848,7 @@ def run_hsp(args):
         A = (gen.csr_uniform if layout == "uniform" else gen.csr_powerlaw)(n, n, sp, seed=seed)
         rp, ci, v = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.colidx, A.vals))
         plan = gb.HspPlan(rp, ci, v, n)
+        touched = int(np.unique(A.colidx).size)
         g = torch.Generator(device=dev)
         g.manual_seed(seed)
         for N in (32, 64, 128):
@@ -732,11 +863,16 @@ def run_hsp(args):
             launches += (gb.launch_count() - l0) // (args.steps + args.warmup)
             flop_sum += f
             ms_sum += ms
+            comp = compulsory_bytes_spmm(A.nnz, n, touched, N)
             points.append({"n": n, "sparsity": sp, "rows": layout, "N": N, "nnz": A.nnz, **plan.info(),
                            "hsp_ms": round(ms, 4), "gflops": round(f / ms / 1e6, 1),
-                           "gather_gbs": round(nbytes / ms / 1e6, 1), "frac": round(nbytes / ms / 1e6 / peak, 4),
-                           "rowsplit_ms": t(lambda: gb.spmm(rp, ci, v, Bd, out=C, stream=stream)),
-                           "merge_ms": t(lambda: gb.spmm(rp, ci, v, Bd, out=C, variant="merge", stream=stream))})
+                           "hbm_gbs": round(comp / ms / 1e6, 1), "frac": round(comp / ms / 1e6 / peak, 4),
+                           "gather_model_gbs": round(nbytes / ms / 1e6, 1),
+                           "rowsplit_ms": t(lambda: gb.spmm(rp, ci, v, Bd, out=C, variant="rowsplit", stream=stream)),
+                           "merge_ms": t(lambda: gb.spmm(rp, ci, v, Bd, out=C, variant="merge", stream=stream)),
+                           "rowgroup_ms": t(lambda: gb.spmm(rp, ci, v, Bd, out=C, variant="rowgroup", stream=stream)),
+                           "auto_ms": t(lambda: gb.spmm(rp, ci, v, Bd, out=C, stream=stream)),
+                           "auto_variant": gb.auto_choice(rp, n, ci, b_bytes=4 * N * n, row_bytes=4 * N)[0]})
             del Bd, C
         plan.close()
         del A, rp, ci, v
@@ -745,7 +881,9 @@ def run_hsp(args):
           {"workload": "1048576^2 at 99.9999%, 262144^2 at 99.999%, 65536^2 at 99.99% (uniform rows) and 262144^2 "
                        "at 99.99% (power-law rows), values U[-1,1], B N(0,1) FP32, N 32/64/128",
            "l2": "flushed before every timed call (256 MB written)", "points": points},
-          roofline={"bound": "hbm", "kernel": "hsp_kernel, gather model", "peak": peak, "peak_kind": peak_kind,
+          roofline={"bound": "hbm", "kernel": "hsp_kernel, compulsory bytes (every operand once; the B rows read "
+                                         "at least once) with L2 flushed before each call",
+                    "peak": peak, "peak_kind": peak_kind,
                     "unit": "GB/s", "frac_min": min(p["frac"] for p in points),
                     "frac_max": max(p["frac"] for p in points)},
           gpu_launches_per_call=int(launches // max(1, len(points))))
@@ -805,52 +943,86 @@ def run_batched(args):
 
 
 def run_selector(args):
-    """Learned selector: 2,000 training and 200 held-out corpus matrices, labels from the
-    exhaustive autotuner, the MLP trained by the library's kernels; regret vs exhaustive."""
+    """Learned selectors for SpMM and SDDMM: 2,000 training and 200 held-out corpus matrices
+    (rows 4,096..262,144) plus 24 held-out matrices of 1,048,576 rows (outside the training
+    range), labels from the exhaustive autotuners, MLPs trained by the library's kernels.
+    Regret against exhaustive autotuning is reported for the MLP alone and with the
+    fallback (the autotuner run again on the matrix when a feature is out of range or the
+    top two predictions are close), with the fallback rate."""
     import torch
 
     import paper_2604_27985_gb300 as gb
     from paper_2604_27985_gb300 import selector as sel
 
-    n_train, n_test = args.selector_train, args.selector_test
-    feats, times, specs = [], [], []
-    t_label = time.time()
-    for i in range(n_train + n_test):
-        spec = gen.corpus_spec(i, 5000 if i < n_train else 6000)
-        rp, ci, v = gen.corpus_matrix(spec)
-        f, tm = sel.label(rp, ci, v, spec["n"], spec["N"], spec["dtype"], reps=3)
-        feats.append(f.cpu().numpy())
-        times.append(tm)
-        specs.append(spec)
-    t_label = time.time() - t_label
-    feats, times = np.stack(feats), np.asarray(times)
-    model = sel.Selector(seed=0)
-    t0 = time.time()
-    model.fit(feats[:n_train], times[:n_train], steps=args.selector_steps, batch=64, lr=1e-3)
-    torch.cuda.synchronize()
-    t_train = time.time() - t0
-    _, choice = model.predict(feats[n_train:])
-    r = sel.regret(times[n_train:], choice.cpu().numpy())
-    fixed_all = [float(np.mean(sel.regret(times[n_train:], np.full(n_test, v)))) for v in range(gb.N_VARIANTS)]
-    fixed = {"best_single_variant": int(np.argmin(fixed_all)), "best_single_mean": min(fixed_all),
-             "rowsplit_v2_u4": fixed_all[4], "merge_v2_u4": fixed_all[13]}
-    # time of one selection (features + inference) on a held-out matrix
-    spec = specs[n_train]
-    rp, ci, v = gen.corpus_matrix(spec)
-    ms_sel = _event_ms(lambda: model.choose(rp, ci, spec["n"], spec["N"], spec["dtype"]), 20, 3,
-                       torch.cuda.current_stream())
-    if args.selector_save:
-        model.save(args.selector_save, regret_mean=float(r.mean()), regret_p90=float(np.quantile(r, 0.9)),
-                   regret_max=float(r.max()), train=n_train, test=n_test)
-    _line("selector regret vs exhaustive autotuning (mean t_chosen/t_best - 1)", float(r.mean()), "fraction",
-          ms_sel, args, "f32",
-          {"workload": f"corpus of {n_train} training + {n_test} held-out matrices (rows log-uniform "
-                       "[4096, 262144], sparsity 90/99/99.9%, uniform/power-law/banded/block, N 32..512, "
-                       "FP32/BF16), 24 SpMM variants", "redraws": int(sum(s["redraws"] for s in specs))},
-          higher_is_better=False, regret={"mean": float(r.mean()), "p50": float(np.median(r)),
-                                          "p90": float(np.quantile(r, 0.9)), "max": float(r.max()),
-                                          "fixed_choices_mean": fixed},
-          seconds={"labels": round(t_label, 1), "train": round(t_train, 2)}, selection_ms=round(ms_sel, 4))
+    n_train, n_test, n_ext = args.selector_train, args.selector_test, args.selector_extrapolate
+    specs = ([gen.corpus_spec(i, 5000) for i in range(n_train)] + [gen.corpus_spec(i, 6000) for i in range(n_test)]
+             + [gen.extrapolation_spec(i, 7000) for i in range(n_ext)])
+    results, t_total = {}, {}
+    stream = torch.cuda.current_stream()
+    for op in ("spmm", "sddmm"):
+        t0 = time.time()
+        feats, times = [], []
+        for spec in specs:
+            rp, ci, v = gen.corpus_matrix(spec)
+            f, tm = sel.label(rp, ci, v, spec["n"], spec["N"], spec["dtype"], reps=3, op=op)
+            feats.append(f.cpu().numpy())
+            times.append(tm)
+            del rp, ci, v
+        t_label = time.time() - t0
+        feats, times = np.stack(feats), np.asarray(times)
+        model = sel.Selector(seed=0, op=op, margin=args.selector_margin, gap=args.selector_gap)
+        t0 = time.time()
+        model.fit(feats[:n_train], times[:n_train], steps=args.selector_steps, batch=64, lr=1e-3)
+        torch.cuda.synchronize()
+        t_train = time.time() - t0
+        evals = {}
+        for name, lo, hi in (("held_out", n_train, n_train + n_test), ("extrapolation", n_train + n_test, len(specs))):
+            if hi <= lo:
+                continue
+            mlp, fb, reasons = [], [], {"range": 0, "gap": 0}
+            for k in range(lo, hi):
+                spec = specs[k]
+                rp, ci, _ = gen.corpus_matrix(spec)
+                v_mlp = model.choose(rp, ci, spec["n"], spec["N"], spec["dtype"], fallback=False)
+                before = dict(model.counts)
+                v_fb = model.choose(rp, ci, spec["n"], spec["N"], spec["dtype"], fallback=True)
+                for r in reasons:
+                    reasons[r] += model.counts[r] - before[r]
+                mlp.append(v_mlp)
+                fb.append(v_fb)
+                del rp, ci
+            r_mlp, r_fb = sel.regret(times[lo:hi], mlp), sel.regret(times[lo:hi], fb)
+            stat = lambda r: {"mean": float(r.mean()), "p50": float(np.median(r)), "p90": float(np.quantile(r, 0.9)),
+                              "max": float(r.max())}
+            evals[name] = {"matrices": hi - lo, "regret_mlp_only": stat(r_mlp), "regret_with_fallback": stat(r_fb),
+                           "fallback_rate": round((reasons["range"] + reasons["gap"]) / (hi - lo), 4),
+                           "fallback_reasons": reasons}
+        nv = gb.N_SDDMM_VARIANTS if op == "sddmm" else gb.N_VARIANTS
+        fixed_all = [float(np.mean(sel.regret(times[n_train:n_train + n_test], np.full(n_test, v))))
+                     for v in range(nv)]
+        # time of one selection (features + inference) on a held-out matrix
+        spec = specs[n_train]
+        rp, ci, _ = gen.corpus_matrix(spec)
+        ms_sel = _event_ms(lambda: model.choose(rp, ci, spec["n"], spec["N"], spec["dtype"], fallback=False), 20, 3,
+                           stream)
+        results[op] = {**evals, "best_single_variant": int(np.argmin(fixed_all)),
+                       "best_single_variant_regret_mean": min(fixed_all), "selection_ms": round(ms_sel, 4),
+                       "seconds": {"labels": round(t_label, 1), "train": round(t_train, 2)}}
+        if args.selector_save:
+            base = args.selector_save + ("_sddmm" if op == "sddmm" else "")
+            model.save(base, regret_mean=evals["held_out"]["regret_with_fallback"]["mean"],
+                       regret_mlp_only_mean=evals["held_out"]["regret_mlp_only"]["mean"], train=n_train, test=n_test)
+        t_total[op] = t_label + t_train
+    head = results["spmm"]["held_out"]["regret_with_fallback"]["mean"]
+    _line("selector regret vs exhaustive autotuning (mean t_chosen/t_best - 1, with fallback)", head, "fraction",
+          results["spmm"]["selection_ms"], args, "f32",
+          {"workload": f"corpus of {n_train} training + {n_test} held-out matrices (rows log-uniform [4096, 262144], "
+                       "sparsity 90/99/99.9%, uniform/power-law/banded/block, N 32..512, FP32/BF16) and "
+                       f"{n_ext} held-out 1048576-row matrices (99.99..99.9999%); 24 SpMM variants (incl. row groups "
+                       "and the hyper-sparse plan), 9 SDDMM variants",
+           "redraws": int(sum(s_["redraws"] for s_ in specs)),
+           "fallback": {"margin": args.selector_margin, "gap": args.selector_gap}},
+          higher_is_better=False, selectors=results)
 
 
 def _sub(A, r0, r1):
@@ -963,6 +1135,9 @@ def main():
     ap.add_argument("--selector-test", type=int, default=200)
     ap.add_argument("--selector-steps", type=int, default=6000)
     ap.add_argument("--selector-save", default="")
+    ap.add_argument("--selector-extrapolate", type=int, default=24)
+    ap.add_argument("--selector-margin", type=float, default=0.1)
+    ap.add_argument("--selector-gap", type=float, default=0.02)
     ap.add_argument("--write-traffic", nargs=3, metavar=("REPORT", "SPMM_RE", "SDDMM_RE"),
                     help="store per-launch DRAM bytes from an ncu report and exit")
     args = ap.parse_args()

@@ -66,8 +66,8 @@ GBSP_EXPORT int gbsp_gather_probe(const void *table, int64_t rows, int64_t row_b
                                   void *stream) {
     if (!table || !idx || !sink || rows <= 0 || n < 0 || blocks <= 0)
         return fail(GBSP_ERR_INVALID_ARG, "gather probe: bad argument");
-    if (row_bytes != 128 && row_bytes != 256 && row_bytes != 512)
-        return fail(GBSP_ERR_UNSUPPORTED, "gather probe: row_bytes must be 128, 256 or 512");
+    if (row_bytes != 128 && row_bytes != 256 && row_bytes != 512 && row_bytes != 1024)
+        return fail(GBSP_ERR_UNSUPPORTED, "gather probe: row_bytes must be 128, 256, 512 or 1024");
     if (ld_bytes < row_bytes || ld_bytes % 16 || !aligned16(table))
         return fail(GBSP_ERR_ALIGN, "gather probe: the table must be 16-byte aligned with ld_bytes a multiple of 16");
     if (n == 0) return ok();
@@ -77,7 +77,9 @@ GBSP_EXPORT int gbsp_gather_probe(const void *table, int64_t rows, int64_t row_b
         st = launch_probe<8, 1>(table, ld_bytes, idx, n, sink, blocks, unroll, s);
     else if (row_bytes == 256)
         st = launch_probe<8, 2>(table, ld_bytes, idx, n, sink, blocks, unroll, s);
-    else
+    else if (row_bytes == 512)
         st = launch_probe<16, 2>(table, ld_bytes, idx, n, sink, blocks, unroll, s);
+    else
+        st = launch_probe<32, 2>(table, ld_bytes, idx, n, sink, blocks, unroll, s);
     return st ? st : ok();
 }

@@ -46,3 +46,21 @@ def test_reference_arm_line():
     assert line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert line["config"]["nnz"] == 42_949_673
+
+
+def test_l2_roofline_fields():
+    """The L2 roof holds the gathered-row bytes of one launch against the gather probe, and
+    reports the HBM fraction on compulsory bytes beside it (figures from one GB300 run:
+    SpMM 0.515 ms, probe 21,187.7 GB/s over 256-byte rows)."""
+    import bench
+
+    nnz = 42_949_673
+    r = bench.l2_roofline("spmm", nnz, 256, 21187.7, 0.515, 6663.2, "measured", 377_413_964, 11_355_753_032, None)
+    assert r["bound"] == "l2" and r["unit"] == "GB/s" and r["peak"] == 21187.7
+    assert r["algorithmic_bytes_per_launch"] == nnz * 256
+    assert abs(r["achieved"] - 21349.6) < 0.2 and abs(r["frac"] - 1.0076) < 1e-4
+    assert abs(r["hbm"]["achieved"] - 732.8) < 0.1 and abs(r["hbm"]["frac"] - 0.11) < 1e-3
+    # every fraction is a fraction of the peak it names
+    assert r["frac"] == round(r["achieved"] / r["peak"], 4)
+    # SDDMM compulsory bytes: row pointers, index + value + output per entry, X and Y once
+    assert bench.compulsory_bytes_sddmm(nnz, 65_536, 65_536, 32) == 4 * 65_537 + 12 * nnz + 2 * 65_536 * 32 * 4

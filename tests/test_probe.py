@@ -26,7 +26,7 @@ def _expected(table_u32, idx, row_words):
     return np.uint32(acc)
 
 
-@pytest.mark.parametrize("row_bytes,ld_words", [(128, 32), (256, 64), (512, 128), (256, 72)])
+@pytest.mark.parametrize("row_bytes,ld_words", [(128, 32), (256, 64), (512, 128), (256, 72), (1024, 256), (1024, 264)])
 @pytest.mark.parametrize("unroll", [4, 8])
 @pytest.mark.parametrize("n", [1, 31, 32, 1000, 100003])
 def test_probe_reads_every_row(gb, row_bytes, ld_words, unroll, n):
