@@ -22,4 +22,4 @@ from .csr import (  # noqa: F401
     dense_int,
     vals_int,
 )
-from .corpus import corpus_matrix, corpus_spec  # noqa: F401
+from .corpus import corpus_matrix, corpus_spec, extrapolation_spec  # noqa: F401

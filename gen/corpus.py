@@ -40,6 +40,20 @@ def corpus_spec(index: int, seed: int, max_nnz: int = 1 << 24, max_work: int = 1
             "nnz_target": T, "redraws": redraws}
 
 
+def extrapolation_spec(index: int, seed: int) -> dict:
+    """A held-out matrix outside the corpus's range of rows: 1,048,576 x 1,048,576 at 99.99%,
+    99.999% or 99.9999% sparsity, one of the four structures, N in {32, 64, 128}, FP32 or
+    BF16 (drawn from (seed, index) as corpus_spec draws)."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([int(seed), int(index), 13])))
+    n = 1 << 20
+    sp = float(rng.choice((0.9999, 0.99999, 0.999999)))
+    st = str(rng.choice(STRUCTURES))
+    N = int(rng.choice((32, 64, 128)))
+    dt = int(rng.integers(0, 2))
+    return {"index": index, "seed": seed, "n": n, "sparsity": sp, "structure": st, "N": N, "dtype": dt,
+            "nnz_target": nnz_for(n, n, sp), "redraws": 0}
+
+
 def corpus_matrix(spec: dict, device="cuda"):
     """(rowptr, colidx, vals) torch tensors on the device for one corpus entry."""
     import torch

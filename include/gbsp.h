@@ -56,14 +56,19 @@ typedef enum {
     GBSP_E4M3 = 2  /* FP8 E4M3 (OCP), stored as uint8 codes, with one FP32 scale per row */
 } gbsp_dtype;
 
-/* Kernel variants of SpMM / SDDMM.  AUTO lets the library choose. */
+/* Kernel variants of SpMM / SDDMM.  AUTO lets the library choose (see spmm_csr_ex and
+ * sddmm_csr_ex for how). */
 typedef enum {
     GBSP_VARIANT_AUTO = 0,
     GBSP_VARIANT_ROWSPLIT = 1, /* one warp per row, vectorised gathers */
     GBSP_VARIANT_MERGE = 2,    /* nnz-balanced merge-path split with a carry fix-up pass */
     GBSP_VARIANT_SCALAR = 3,   /* unvectorised, any width / alignment */
-    GBSP_VARIANT_ENTRY = 4     /* SDDMM only: stored entries split evenly across warps regardless of
+    GBSP_VARIANT_ENTRY = 4,    /* SDDMM only: stored entries split evenly across warps regardless of
                                   rows (short or skewed rows); GBSP_ERR_UNSUPPORTED for SpMM */
+    GBSP_VARIANT_ROWGROUP = 5, /* SpMM only: several consecutive rows per warp, one lane group each
+                                  (rows of a few entries); GBSP_ERR_UNSUPPORTED for SDDMM */
+    GBSP_VARIANT_HSP_PLAN = 6  /* a selector label only: the hyper-sparse plan (gbsp_hsp_plan_*);
+                                  spmm_csr_ex returns GBSP_ERR_UNSUPPORTED for it */
 } gbsp_variant;
 
 /* A sparse matrix in CSR form (all pointers device). */
@@ -113,7 +118,21 @@ int sddmm_csr(const int32_t *rowptr, const int32_t *colidx, const float *svals, 
  * Supported dtype pairs (A, B) -> C: (F32, F32) -> F32, (BF16, BF16) -> F32 and
  * (E4M3, E4M3) -> F32 with per-row scales on both A (s_i) and B (t_k):
  *   C[i, n] = s_i * sum_p qa_p * t_{colidx[p]} * qb[colidx[p], n].
- * Accumulation is FP32 in every form.  B->rows must equal A->cols, C is A->rows x B->cols. */
+ * Accumulation is FP32 in every form.  B->rows must equal A->cols, C is A->rows x B->cols.
+ * GBSP_VARIANT_AUTO balances the work by the pattern's row lengths (load balancing across
+ * uneven rows, Section II-D): rows averaging under 12 entries with none past 128 take the
+ * row groups, skewed rows (coefficient of variation above 1, or a longest row past 16
+ * times the mean and past 256) the merge path, even rows gathered from a B of more than
+ * 192 MB (past L2) in rows of at least 256 bytes the row groups, the rest the row split;
+ * unvectorisable operands take the scalar kernel.  The row statistics come from one integer pass over
+ * rowptr.  The first AUTO call on a pattern measures it and waits for the result (a
+ * synchronisation); the choice is kept per (device, rowptr, colidx, rows, cols) for the
+ * process (64 patterns, oldest dropped first).  Each later call uses the kept choice and
+ * queues one more pass (a small kernel and a copy to pinned memory on the stream, no
+ * wait); the next call adopts its result once it has arrived, so another pattern placed at
+ * the same addresses gets its own choice from its second call on.  A stale choice costs
+ * speed, never correctness.  Under stream capture nothing is queued: a kept choice is used,
+ * else the row split.  gbsp_auto_choice reports the choice; gbsp_auto_forget drops them. */
 int spmm_csr_ex(const gbsp_csr *A, const gbsp_dense *B, gbsp_dense *C, const gbsp_opts *opts,
                 void *stream);
 
@@ -121,9 +140,28 @@ int spmm_csr_ex(const gbsp_csr *A, const gbsp_dense *B, gbsp_dense *C, const gbs
  * Supported (S, X, Y): all F32; S F32 with X, Y BF16; S F32 with X, Y E4M3 (per-row
  * scales u_i on X and v_j on Y: out[p] = s_p * u_i * v_j * <qx_i, qy_j>).
  * out is float[S->nnz] in CSR order.  X->rows = S->rows, Y->rows = S->cols,
- * X->cols = Y->cols = Kd. */
+ * X->cols = Y->cols = Kd.  GBSP_VARIANT_AUTO takes the entry split when rows average under 32
+ * stored entries, the merge path on skewed rows (coefficient of variation above 1, or a
+ * longest row past 16 times the mean and past 256) and the row split otherwise, from the
+ * same kept row statistics as spmm_csr_ex's AUTO (measured, kept and re-measured as
+ * described there); unvectorisable operands take the scalar kernel. */
 int sddmm_csr_ex(const gbsp_csr *S, const gbsp_dense *X, const gbsp_dense *Y, float *out,
                  const gbsp_opts *opts, void *stream);
+
+/* The split GBSP_VARIANT_AUTO takes on A's pattern (vectorisable operands) for op 0, SpMM
+ * (GBSP_VARIANT_ROWSPLIT, _MERGE or _ROWGROUP), or op 1, SDDMM (GBSP_VARIANT_ROWSPLIT, _MERGE
+ * or _ENTRY), with a gathered dense operand (B, or Y) of b_bytes bytes in rows of row_bytes
+ * bytes (0 and 0 when unknown), written to *variant (host); GBSP_ERR_INVALID_ARG for another
+ * op.  stats (host, may be NULL)
+ * receives the statistics behind it: {rows, stored entries, sum of squared row lengths,
+ * longest row, empty rows}, or -1s for an unmeasured pattern under stream capture.  It is
+ * an AUTO call without the product: a new pattern is measured at once (synchronises the
+ * stream), a kept one answers from its kept choice and queues a re-measurement.  Only
+ * rowptr of A is read. */
+int gbsp_auto_choice(const gbsp_csr *A, int32_t op, int64_t b_bytes, int64_t row_bytes, void *stream,
+                     int32_t *variant, int64_t *stats);
+/* Drops every choice GBSP_VARIANT_AUTO has kept (the next AUTO call measures again). */
+void gbsp_auto_forget(void);
 
 /* Checks a CSR on the device: rowptr[0] = 0, rowptr non-decreasing, rowptr[rows] = nnz,
  * 0 <= colidx < cols.  Writes the number of violations to *n_bad (host pointer) and
@@ -329,14 +367,46 @@ int gbsp_hsp_plan_execute(const gbsp_hsp_plan *plan, const gbsp_dense *B, gbsp_d
 int gbsp_hsp_plan_info(const gbsp_hsp_plan *plan, int64_t *info, int n);
 void gbsp_hsp_plan_destroy(gbsp_hsp_plan *plan);
 
+/* ---- SELL-C-sigma SpMM (sliced, padded, column-major) ------------------------------------ */
+
+/* SpMM, Eq. 1, C = A B for FP32 A (M x K, CSR) and B (K x N), through SELL-C-sigma: the
+ * sliced padded format of the paper's SELLPACK-like stream (Section III-A) and of its
+ * future work on formats (Section V).  gbsp_sell_plan_create checks A as gbsp_csr_validate
+ * does (nnz must be given; GBSP_ERR_INVALID_CSR), reads rowptr to the host (synchronises
+ * the stream), sorts the rows by decreasing length within windows of sigma rows (sigma <= 0
+ * or > M: one window; else a multiple of C), cuts the sorted rows into slices of C rows
+ * (C <= 0: 64; a multiple of 8, at most 1024), pads each slice to its longest row and
+ * stores it column-major (entry j of the slice's row r at slot j * C + r) in the plan's own
+ * device arrays: the row order and lengths (int32 each per row), the slice offsets (int64)
+ * and the slots (int32 column and FP32 value each, padding included).  A may be freed
+ * after creation.
+ * gbsp_sell_plan_execute: one lane group per row, several rows per warp, every group
+ * stopping at its own row's length (padding is never read); B float[K x N] (ld >= N), C
+ * float[M x N] (ld >= N, overwritten); N and both ld multiples of 4, B and C 16-byte
+ * aligned (GBSP_ERR_ALIGN otherwise); C must be a multiple of 8 x (rows per warp), which
+ * holds for the default C = 64 from N = 16 on (GBSP_ERR_UNSUPPORTED otherwise).  One launch,
+ * asynchronous; each row's sum runs in its stored order.
+ * gbsp_sell_plan_info fills {slices, C, sigma, slots including padding, nnz}. */
+typedef struct gbsp_sell_plan gbsp_sell_plan;
+int gbsp_sell_plan_create(const gbsp_csr *A, int32_t C, int32_t sigma, void *stream, gbsp_sell_plan **out);
+int gbsp_sell_plan_execute(const gbsp_sell_plan *plan, const gbsp_dense *B, gbsp_dense *C, void *stream);
+int gbsp_sell_plan_info(const gbsp_sell_plan *plan, int64_t *info, int n);
+void gbsp_sell_plan_destroy(gbsp_sell_plan *plan);
+
 /* ---- kernel selection: features, autotuner, MLP ------------------------------------------- */
 
 /* The 24 SpMM variants the selector chooses among, as options for spmm_csr_ex:
  *   0..8   row-split, vecs {1,2,4} x unroll {2,4,8}     (index = 3 * vecs_index + unroll_index)
  *   9..17  merge path, the same nine layouts
  *   18..21 merge path with 1 or 2 CTAs per SM, vecs {1,2}, unroll 4
- *   22     unvectorised; 23 row-split with vecs 1, unroll 1. */
+ *   22     row groups (GBSP_VARIANT_ROWGROUP), default layout
+ *   23     the hyper-sparse plan: out->variant = GBSP_VARIANT_HSP_PLAN, meaning "create a
+ *          gbsp_hsp_plan of A once and execute it" (FP32 only); not an spmm_csr_ex option. */
 int gbsp_variant_opts(int variant, gbsp_opts *out);
+/* The SDDMM variants (Eq. 2) the SDDMM selector chooses among, as options for sddmm_csr_ex:
+ * index = 3 * split + vecs_index, split 0 row split, 1 merge path, 2 entry split, vecs
+ * {1, 2, 4}; 9 variants (indices 0..8), GBSP_ERR_INVALID_ARG beyond. */
+int gbsp_sddmm_variant_opts(int variant, gbsp_opts *out);
 
 /* 16 features of a CSR matrix for a dense width N and dtype, written to feats (device,
  * float[16]) in one pass over rowptr / colidx (asynchronous):
@@ -366,36 +436,45 @@ int gbsp_mlp_train(float *weights, float *adam, const float *norm, const float *
                    const float *mask, const int32_t *order, int norder, int steps, int batch, float lr, int t0,
                    void *stream);
 
-/* Times every variant of spmm_csr_ex on A, B, C (one untimed call, then reps timed calls
- * with CUDA events) and writes times_ms[24] (host; INFINITY where a variant does not apply)
- * and *best (host).  Synchronises the stream; C ends up holding the last variant's result. */
+/* Times every SpMM variant of gbsp_variant_opts on A, B, C (one untimed call, then reps
+ * timed calls with CUDA events; variant 23 builds a hyper-sparse plan of A first, outside
+ * the timed calls, so A->nnz must be given) and writes times_ms[24] (host; INFINITY where a
+ * variant does not apply) and *best (host).  Synchronises the stream; C ends up holding the
+ * last variant's result. */
 int gbsp_autotune(const gbsp_csr *A, const gbsp_dense *B, gbsp_dense *C, int reps, float *times_ms,
                   int32_t *best, void *stream);
+/* The same for SDDMM: times the 9 variants of gbsp_sddmm_variant_opts on S, X, Y, out and
+ * writes times_ms[24] (INFINITY at indices 9..23 and where a variant does not apply) and
+ * *best.  Synchronises the stream; out ends up holding the last variant's result. */
+int gbsp_autotune_sddmm(const gbsp_csr *S, const gbsp_dense *X, const gbsp_dense *Y, float *out, int reps,
+                        float *times_ms, int32_t *best, void *stream);
 
 /* ---- allocation-free variant ---------------------------------------------------------- */
 
 /* The paper has no counterpart of this entry point.  It serves callers that must not
  * allocate device memory during a call: a process whose HBM is already handed out by
- * another allocator (so an allocation can fail at call time), a latency-bound loop that
- * cannot absorb an allocation, code recorded into a CUDA graph that must hold no
- * allocation nodes.
+ * another allocator (a framework's caching allocator, or a fixed arena in a serving
+ * process), where an allocation can fail at call time, and a latency-bound loop that
+ * cannot absorb an allocation and the synchronisation it may bring.
  * FP32 SpMM with the meaning of spmm_csr (Eq. 1; rowptr, colidx, vals, B, C device; B and
  * C with ld = N; C overwritten), on the given stream, through the merge-path kernels.
  * Their carry buffers live in one fixed 4 MiB device array owned by the library, which
  * every GPU that loads the library holds until the process exits; nothing is allocated.
  * Limits: N <= 1024 and a multiple of 4, B and C 16-byte aligned; a larger N returns
  * GBSP_ERR_INVALID_ARG, misalignment GBSP_ERR_ALIGN.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) with that device current: make that
- * first call before any stream capture.  All calls share the one array, so calls that can
- * overlap on the GPU (unordered streams) race and must be serialised by the caller.  Each
- * call writes every scratch element before reading it, so what a previous call left there
- * does not matter. */
+ * the array's device address (cudaGetSymbolAddress) with that device current and keeps it
+ * for the life of the process: make that first call before any stream capture.
+ * cudaDeviceReset destroys the array with the device's context and leaves the kept address
+ * stale, so do not call this entry point on a device after resetting it.  All calls share
+ * the one array, so calls that can overlap on the GPU (unordered streams) race and must be
+ * serialised by the caller.  Each call writes every scratch element before reading it, so
+ * what a previous call left there does not matter. */
 int spmm_csr_noalloc(const int32_t *rowptr, const int32_t *colidx, const float *vals, const float *B,
                      float *C, int64_t M, int64_t K, int64_t N, void *stream);
 
 /* ---- measurement utility (no counterpart in the paper) ------------------------------- */
 
-/* Gather-bandwidth probe: reads the rows table[idx[p]] (row_bytes = 128, 256 or 512 bytes
+/* Gather-bandwidth probe: reads the rows table[idx[p]] (row_bytes = 128, 256, 512 or 1024 bytes
  * each, consecutive rows ld_bytes apart) for p in [0, n) with the lane layout of the
  * SpMM / SDDMM kernels (16-byte vectors, several rows in flight per lane, indices loaded
  * coalesced and shuffled to the lane groups) and no arithmetic but an XOR per vector, so

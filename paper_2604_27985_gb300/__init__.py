@@ -12,6 +12,9 @@ from .ops import (  # noqa: F401
     N_PARAMS,
     N_VARIANTS,
     autotune,
+    autotune_sddmm,
+    sddmm_variant_options,
+    N_SDDMM_VARIANTS,
     feature_norm,
     features,
     gather_probe,
@@ -22,8 +25,11 @@ from .ops import (  # noqa: F401
     gnn_sddmm_spmm_batched,
     gnn_gat_batched,
     HspPlan,
+    SellPlan,
     KbinPlan,
     TcPlan,
+    auto_choice,
+    auto_forget,
     csr_validate,
     launch_count,
     quantize_bf16,

@@ -23,7 +23,7 @@ STATUS = {
     -7: "GBSP_ERR_TIMEOUT",
 }
 F32, BF16, E4M3 = 0, 1, 2
-VARIANTS = {"auto": 0, "rowsplit": 1, "merge": 2, "scalar": 3, "entry": 4}
+VARIANTS = {"auto": 0, "rowsplit": 1, "merge": 2, "scalar": 3, "entry": 4, "rowgroup": 5}
 
 
 class GbspError(RuntimeError):
@@ -64,6 +64,8 @@ def _load() -> ctypes.CDLL:
         "sddmm_csr_ex": [ctypes.POINTER(Csr), ctypes.POINTER(Dense), ctypes.POINTER(Dense), P,
                          ctypes.POINTER(Opts), P],
         "gbsp_csr_validate": [ctypes.POINTER(Csr), P, ctypes.POINTER(ctypes.c_int64)],
+        "gbsp_auto_choice": [ctypes.POINTER(Csr), ctypes.c_int32, I64, I64, P, ctypes.POINTER(ctypes.c_int32),
+                             ctypes.POINTER(I64)],
         "gbsp_quantize_bf16": [P, P, I64, P],
         "gbsp_quantize_e4m3_rows": [P, P, I64, I64, I64, P, P, P],
         "gbsp_plan_create": [ctypes.POINTER(Csr), ctypes.c_int32, ctypes.POINTER(Opts), P, ctypes.POINTER(P)],
@@ -84,10 +86,16 @@ def _load() -> ctypes.CDLL:
         "gbsp_kbin_plan_create": [ctypes.POINTER(Csr), I64, I64, P, ctypes.POINTER(P)],
         "gbsp_kbin_plan_execute": [P, ctypes.POINTER(Dense), ctypes.POINTER(Dense), P],
         "gbsp_kbin_plan_info": [P, ctypes.POINTER(I64), I],
+        "gbsp_sell_plan_create": [ctypes.POINTER(Csr), ctypes.c_int32, ctypes.c_int32, P, ctypes.POINTER(P)],
+        "gbsp_sell_plan_execute": [P, ctypes.POINTER(Dense), ctypes.POINTER(Dense), P],
+        "gbsp_sell_plan_info": [P, ctypes.POINTER(I64), I],
         "gbsp_hsp_plan_create": [ctypes.POINTER(Csr), P, ctypes.POINTER(P)],
         "gbsp_hsp_plan_execute": [P, ctypes.POINTER(Dense), ctypes.POINTER(Dense), P],
         "gbsp_hsp_plan_info": [P, ctypes.POINTER(I64), I],
         "gbsp_variant_opts": [I, ctypes.POINTER(Opts)],
+        "gbsp_sddmm_variant_opts": [I, ctypes.POINTER(Opts)],
+        "gbsp_autotune_sddmm": [ctypes.POINTER(Csr), ctypes.POINTER(Dense), ctypes.POINTER(Dense), P, I,
+                                ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int32), P],
         "gbsp_features": [ctypes.POINTER(Csr), I64, ctypes.c_int32, P, P],
         "gbsp_feature_norm": [P, I, P, P],
         "gbsp_mlp_predict": [P, P, P, I, P, P, P],
@@ -111,8 +119,12 @@ def _load() -> ctypes.CDLL:
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = I
+    lib.gbsp_auto_forget.argtypes = []
+    lib.gbsp_auto_forget.restype = None
     lib.gbsp_batch_plan_destroy.argtypes = [P]
     lib.gbsp_batch_plan_destroy.restype = None
+    lib.gbsp_sell_plan_destroy.argtypes = [P]
+    lib.gbsp_sell_plan_destroy.restype = None
     lib.gbsp_hsp_plan_destroy.argtypes = [P]
     lib.gbsp_hsp_plan_destroy.restype = None
     lib.gbsp_kbin_plan_destroy.argtypes = [P]

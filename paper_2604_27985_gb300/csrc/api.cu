@@ -178,13 +178,19 @@ GBSP_EXPORT int spmm_csr_ex(const gbsp_csr *A, const gbsp_dense *B, gbsp_dense *
     if (injected_fault() == 2) return fail(GBSP_ERR_CUDA, "spmm: injected launch failure (GBSP_FAULT=launch)");
     const bool vec = vec_ok(B) && aligned16(C->data) && C->ld % 4 == 0;
     int variant = o.variant;
-    if (variant == GBSP_VARIANT_AUTO) variant = vec ? GBSP_VARIANT_ROWSPLIT : GBSP_VARIANT_SCALAR;
+    if (variant == GBSP_VARIANT_AUTO) {
+        variant = GBSP_VARIANT_SCALAR;
+        const int64_t rb = B->cols * elem_bytes(B->dtype);
+        if (vec && (st = auto_choice(*A, kOpSpmm, B->rows * rb, rb, s, &variant, nullptr))) return st;
+    }
     if (variant != GBSP_VARIANT_SCALAR && !vec)
         return fail(GBSP_ERR_ALIGN, "spmm: vectorised variant needs 16-byte aligned B and C, and N and ld "
                                     "multiples of %d", elems_per_vec(B->dtype));
     if (variant == GBSP_VARIANT_ENTRY)
         return fail(GBSP_ERR_UNSUPPORTED, "spmm: the entry split is an SDDMM variant (SpMM rows need one owner)");
-    if (variant < GBSP_VARIANT_ROWSPLIT || variant > GBSP_VARIANT_SCALAR)
+    if (variant == GBSP_VARIANT_HSP_PLAN)
+        return fail(GBSP_ERR_UNSUPPORTED, "spmm: the hyper-sparse plan runs through gbsp_hsp_plan_execute");
+    if (variant < GBSP_VARIANT_ROWSPLIT || variant > GBSP_VARIANT_ROWGROUP)
         return fail(GBSP_ERR_INVALID_ARG, "spmm: unknown variant %d", variant);
     SpmmProblem p{};
     p.M = (int32_t)A->rows;
@@ -230,13 +236,16 @@ GBSP_EXPORT int sddmm_csr_ex(const gbsp_csr *S, const gbsp_dense *X, const gbsp_
     const int V = elems_per_vec(X->dtype);
     const bool vec = vec_ok(X) && vec_ok(Y) && X->cols > 0 && X->cols <= 32 * 16;
     int variant = o.variant;
-    // rows shorter than a 32-entry chunk on average leave lanes idle in the row split
-    if (variant == GBSP_VARIANT_AUTO)
-        variant = !vec ? GBSP_VARIANT_SCALAR
-                       : (S->nnz >= 0 && S->nnz < 32 * S->rows ? GBSP_VARIANT_ENTRY : GBSP_VARIANT_ROWSPLIT);
+    if (variant == GBSP_VARIANT_AUTO) {
+        variant = GBSP_VARIANT_SCALAR;
+        const int64_t rb = Y->cols * elem_bytes(Y->dtype);
+        if (vec && (st = auto_choice(*S, kOpSddmm, Y->rows * rb, rb, s, &variant, nullptr))) return st;
+    }
     if (variant != GBSP_VARIANT_SCALAR && !vec)
         return fail(GBSP_ERR_ALIGN, "sddmm: vectorised variant needs 16-byte aligned X and Y, Kd and ld "
                                     "multiples of %d and Kd <= %d", V, 32 * 16);
+    if (variant == GBSP_VARIANT_ROWGROUP || variant == GBSP_VARIANT_HSP_PLAN)
+        return fail(GBSP_ERR_UNSUPPORTED, "sddmm: the row groups and the hyper-sparse plan are SpMM variants");
     if (variant < GBSP_VARIANT_ROWSPLIT || variant > GBSP_VARIANT_ENTRY)
         return fail(GBSP_ERR_INVALID_ARG, "sddmm: unknown variant %d", variant);
     SddmmProblem p{};

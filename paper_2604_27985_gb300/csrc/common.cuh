@@ -53,6 +53,21 @@ struct F32 {
     }
     __device__ __forceinline__ static float value(float v) { return v; }
     __device__ __forceinline__ static float scalar(const stored *p) { return *p; }
+    // acc[k] += a * element k of the vector r (single-rounding fmaf per element)
+    __device__ __forceinline__ static void axpy(float a, const uint4 &r, float (&acc)[4]) {
+        float o[4];
+        unpack(r, o);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k] = fmaf(a, o[k], acc[k]);
+    }
+    // sum + <x, y> over one vector, element by element in order (x decoded as xf, packed as xr)
+    __device__ __forceinline__ static float dot(const uint4 &xr, const float (&xf)[4], const uint4 &yr, float sum) {
+        float y[4];
+        unpack(yr, y);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sum = fmaf(xf[k], y[k], sum);
+        return sum;
+    }
 };
 
 struct BF16 {
@@ -69,6 +84,39 @@ struct BF16 {
     }
     __device__ __forceinline__ static float value(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
     __device__ __forceinline__ static float scalar(const stored *p) { return value(*p); }
+    // acc[k] += a * element k of the vector r, where a must hold a BF16 value (its low 16
+    // bits zero; every BF16-form coefficient is an A value decoded from BF16).  The product
+    // of two BF16 values is exact in FP32, so the mixed-precision fma (BF16 multiplicands,
+    // FP32 addend and result, one rounding) gives exactly fmaf of the decoded values,
+    // without decoding the eight elements first.
+    __device__ __forceinline__ static void axpy(float a, const uint4 &r, float (&acc)[8]) {
+        const uint32_t ab = __float_as_uint(a) >> 16;
+        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            asm("{\n\t.reg .b16 al, ah, bl, bh;\n\t"
+                "mov.b32 {al, ah}, %2;\n\t"
+                "mov.b32 {bl, bh}, %3;\n\t"
+                "fma.rn.f32.bf16 %0, al, bl, %0;\n\t"
+                "fma.rn.f32.bf16 %1, al, bh, %1;\n\t}"
+                : "+f"(acc[2 * i]), "+f"(acc[2 * i + 1])
+                : "r"(ab), "r"(w[i]));
+    }
+    // sum + <x, y> over one vector, element by element in order, with the mixed-precision
+    // fma on the packed BF16 elements of x and y (exact products, as fmaf of decoded values)
+    __device__ __forceinline__ static float dot(const uint4 &xr, const float (&)[8], const uint4 &yr, float sum) {
+        const uint32_t xw[4] = {xr.x, xr.y, xr.z, xr.w}, yw[4] = {yr.x, yr.y, yr.z, yr.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            asm("{\n\t.reg .b16 xl, xh, yl, yh;\n\t"
+                "mov.b32 {xl, xh}, %1;\n\t"
+                "mov.b32 {yl, yh}, %2;\n\t"
+                "fma.rn.f32.bf16 %0, xl, yl, %0;\n\t"
+                "fma.rn.f32.bf16 %0, xh, yh, %0;\n\t}"
+                : "+f"(sum)
+                : "r"(xw[i]), "r"(yw[i]));
+        return sum;
+    }
 };
 
 struct E4M3 {
@@ -96,6 +144,30 @@ struct E4M3 {
         return __half2float(*reinterpret_cast<__half *>(&h));
     }
     __device__ __forceinline__ static float scalar(const stored *p) { return value(*p); }
+    // acc[k] += a * element k of r: the codes decode in pairs (one conversion per two) and
+    // the products go through packed FP32 fmas (two single-rounding fmas per instruction,
+    // each exactly fmaf), which halves the FMA instructions of this ALU-bound form.
+    __device__ __forceinline__ static void axpy(float a, const uint4 &r, float (&acc)[16]) {
+        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+        const float2 aa = make_float2(a, a);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 lo = pair((uint16_t)(w[i] & 0xffffu)), hi = pair((uint16_t)(w[i] >> 16));
+            const float2 r0 = __ffma2_rn(aa, lo, make_float2(acc[4 * i], acc[4 * i + 1]));
+            const float2 r1 = __ffma2_rn(aa, hi, make_float2(acc[4 * i + 2], acc[4 * i + 3]));
+            acc[4 * i] = r0.x;
+            acc[4 * i + 1] = r0.y;
+            acc[4 * i + 2] = r1.x;
+            acc[4 * i + 3] = r1.y;
+        }
+    }
+    __device__ __forceinline__ static float dot(const uint4 &, const float (&xf)[16], const uint4 &yr, float sum) {
+        float y[16];
+        unpack(yr, y);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) sum = fmaf(xf[k], y[k], sum);
+        return sum;
+    }
 };
 
 // Streaming (read-once) loads: indices and values are touched once, so keep them from
@@ -196,6 +268,16 @@ int launch_sddmm_typed(const SddmmProblem &p, int variant, int vecs, cudaStream_
 int launch_spmm(const SpmmProblem &p, int variant, int vecs, int unroll, int ctas_per_sm, cudaStream_t s);
 int launch_sddmm(const SddmmProblem &p, int variant, int vecs, cudaStream_t s);
 int launch_validate(const gbsp_csr &A, unsigned long long *d_count, cudaStream_t s);
+// The split GBSP_VARIANT_AUTO takes for op on A's pattern, from row statistics measured
+// on the first call (synchronising) and re-measured asynchronously on later ones; stats
+// receives {rows, nnz, sum of squared lengths, longest row, empty rows} when non-null.
+// b_bytes and row_bytes describe the gathered dense operand (B of SpMM, Y of SDDMM).
+constexpr int kOpSpmm = 0, kOpSddmm = 1;
+int auto_choice(const gbsp_csr &A, int op, int64_t b_bytes, int64_t row_bytes, cudaStream_t s, int *variant,
+                int64_t *stats);
+int auto_spmm_rule(int64_t M, int64_t nnz, int64_t sumsq, int64_t maxlen, int64_t b_bytes, int64_t row_bytes);
+int auto_sddmm_rule(int64_t M, int64_t nnz, int64_t sumsq, int64_t maxlen);
+void auto_forget_all();
 int launch_quant_bf16(const float *x, uint16_t *out, int64_t n, cudaStream_t s);
 int launch_quant_e4m3_rows(const float *x, const int32_t *rowptr, int64_t nrows, int64_t ncols,
                            int64_t ld, uint8_t *q, float *scale, cudaStream_t s);

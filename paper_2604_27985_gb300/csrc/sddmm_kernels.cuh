@@ -17,8 +17,8 @@ namespace sddmm_detail {
 // Partial dots of one chunk: part[t] is this lane's share of the dot of entry g * LPN + t.
 template <class EL, int LPN, int VPL, bool CHECK_COLS, bool CHECK_NNZ>
 __device__ __forceinline__ void sddmm_chunk(const uint4 *__restrict__ Yv, int64_t ldv, int c, int cnt, int g,
-                                            const bool (&colok)[VPL], const float (&x)[VPL][EL::V],
-                                            float (&part)[LPN]) {
+                                            const bool (&colok)[VPL], const uint4 (&xr)[VPL],
+                                            const float (&x)[VPL][EL::V], float (&part)[LPN]) {
 #pragma unroll
     for (int t = 0; t < LPN; ++t) part[t] = 0.f;
 #pragma unroll
@@ -41,12 +41,7 @@ __device__ __forceinline__ void sddmm_chunk(const uint4 *__restrict__ Yv, int64_
         }
         float sum = 0.f;
 #pragma unroll
-        for (int v = 0; v < VPL; ++v) {
-            float y[EL::V];
-            EL::unpack(raw[v], y);
-#pragma unroll
-            for (int k = 0; k < EL::V; ++k) sum = fmaf(x[v][k], y[k], sum);
-        }
+        for (int v = 0; v < VPL; ++v) sum = EL::dot(xr[v], x[v], raw[v], sum);
         part[t] = sum;
     }
 }
@@ -64,14 +59,15 @@ __device__ __forceinline__ void sddmm_segment(const SddmmProblem &P, int row, in
     const int64_t ldv = P.ldy / EL::V;
 
     bool colok[VPL];
+    uint4 xr[VPL];
     float x[VPL][EL::V];
 #pragma unroll
     for (int v = 0; v < VPL; ++v) {
         const int k0 = (v * LPN + sl) * EL::V;
         colok[v] = !CHECK_COLS || k0 < P.Kd;
-        uint4 raw = make_uint4(0, 0, 0, 0);
-        if (colok[v]) raw = ld_gather16(X + (int64_t)row * P.ldx + k0);
-        EL::unpack(raw, x[v]);
+        xr[v] = make_uint4(0, 0, 0, 0);
+        if (colok[v]) xr[v] = ld_gather16(X + (int64_t)row * P.ldx + k0);
+        EL::unpack(xr[v], x[v]);
     }
     const float xs = EL::dtype == GBSP_E4M3 ? __ldg(P.x_scale + row) : 1.0f;
 
@@ -95,9 +91,9 @@ __device__ __forceinline__ void sddmm_segment(const SddmmProblem &P, int row, in
         }
         float part[LPN];
         if (nb <= p1)
-            sddmm_chunk<EL, LPN, VPL, CHECK_COLS, false>(Yv, ldv, c, 32, g, colok, x, part);
+            sddmm_chunk<EL, LPN, VPL, CHECK_COLS, false>(Yv, ldv, c, 32, g, colok, xr, x, part);
         else
-            sddmm_chunk<EL, LPN, VPL, CHECK_COLS, true>(Yv, ldv, c, (int)(p1 - base), g, colok, x, part);
+            sddmm_chunk<EL, LPN, VPL, CHECK_COLS, true>(Yv, ldv, c, (int)(p1 - base), g, colok, xr, x, part);
 #pragma unroll
         for (int h = LPN / 2; h >= 1; h >>= 1) {
             const bool upper = (sl & h) != 0;

@@ -9,6 +9,7 @@ namespace gbsp {
 namespace sel {
 
 constexpr int kF = 16, kH = 64, kV = 24;
+constexpr int kSddmmVariants = 9;
 constexpr int kW1 = kH * kF, kB1 = kH, kW2 = kH * kH, kB2 = kH, kW3 = kV * kH, kB3 = kV;
 constexpr int kParams = kW1 + kB1 + kW2 + kB2 + kW3 + kB3;  // 6,808
 
@@ -292,8 +293,8 @@ __global__ void __launch_bounds__(256) mlp_train_kernel(float *w, float *adam, c
 //   0..8   row-split, vecs {1,2,4} x unroll {2,4,8}
 //   9..17  merge path, vecs {1,2,4} x unroll {2,4,8}
 //   18..21 merge path with 1 or 2 CTAs per SM, vecs {1,2}, unroll 4
-//   22     unvectorised (any width)
-//   23     row-split, vecs 1, unroll 1
+//   22     row groups (several short rows per warp), default layout
+//   23     the hyper-sparse plan (gbsp_hsp_plan_*; FP32 only), variant GBSP_VARIANT_HSP_PLAN
 int variant_opts(int v, gbsp_opts *o) {
     static const int vecs[3] = {1, 2, 4}, unr[3] = {2, 4, 8};
     *o = gbsp_opts{};
@@ -311,13 +312,11 @@ int variant_opts(int v, gbsp_opts *o) {
         return GBSP_OK;
     }
     if (v == 22) {
-        o->variant = GBSP_VARIANT_SCALAR;
+        o->variant = GBSP_VARIANT_ROWGROUP;
         return GBSP_OK;
     }
     if (v == 23) {
-        o->variant = GBSP_VARIANT_ROWSPLIT;
-        o->vecs = 1;
-        o->unroll = 1;
+        o->variant = GBSP_VARIANT_HSP_PLAN;
         return GBSP_OK;
     }
     return fail(GBSP_ERR_INVALID_ARG, "variant index %d outside 0..23", v);
@@ -396,6 +395,28 @@ GBSP_EXPORT int gbsp_mlp_train(float *weights, float *adam, const float *norm, c
     return st ? st : ok();
 }
 
+namespace {
+
+// Times one variant: an untimed call (which also says whether the variant applies), then
+// reps calls between two events.  Returns false when the variant does not apply.
+template <class F>
+bool time_variant(F call, int reps, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, float *ms_out, int *st) {
+    if (call() != GBSP_OK) return false;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps; ++r) call();
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+        *st = check_launch("autotune");
+        return false;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    *ms_out = ms / reps;
+    return true;
+}
+
+}  // namespace
+
 GBSP_EXPORT int gbsp_autotune(const gbsp_csr *A, const gbsp_dense *B, gbsp_dense *C, int reps, float *times_ms,
                               int32_t *best, void *stream) {
     if (!A || !B || !C || !times_ms || reps < 1) return fail(GBSP_ERR_INVALID_ARG, "autotune: bad arguments");
@@ -408,22 +429,70 @@ GBSP_EXPORT int gbsp_autotune(const gbsp_csr *A, const gbsp_dense *B, gbsp_dense
         gbsp_opts o;
         variant_opts(v, &o);
         times_ms[v] = INFINITY;
-        if (spmm_csr_ex(A, B, C, &o, stream) != GBSP_OK) continue;  // variant not applicable here
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < reps; ++r) spmm_csr_ex(A, B, C, &o, stream);
-        cudaEventRecord(e1, s);
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-            st = check_launch("autotune");
-            break;
-        }
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        times_ms[v] = ms / reps;
+        bool ran;
+        if (o.variant == GBSP_VARIANT_HSP_PLAN) {
+            // the plan is built outside the timed calls, as a caller builds it once per pattern
+            gbsp_hsp_plan *plan = nullptr;
+            if (A->dtype != GBSP_F32 || B->dtype != GBSP_F32 || A->nnz < 0 ||
+                gbsp_hsp_plan_create(A, stream, &plan) != GBSP_OK)
+                continue;
+            ran = time_variant([&] { return gbsp_hsp_plan_execute(plan, B, C, stream); }, reps, s, e0, e1, &ms, &st);
+            gbsp_hsp_plan_destroy(plan);
+        } else {
+            ran = time_variant([&] { return spmm_csr_ex(A, B, C, &o, stream); }, reps, s, e0, e1, &ms, &st);
+        }
+        if (!ran) continue;
+        times_ms[v] = ms;
         if (bi < 0 || times_ms[v] < times_ms[bi]) bi = v;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st) return st;
     if (best) *best = bi;
-    return bi < 0 ? fail(GBSP_ERR_UNSUPPORTED, "autotune: no variant ran") : ok();
+    ok();  // a variant that did not apply left its message; the search itself succeeded
+    return bi < 0 ? fail(GBSP_ERR_UNSUPPORTED, "autotune: no variant ran") : GBSP_OK;
+}
+
+// The SDDMM variants the selector chooses among: index 3 * split + (vecs index), split in
+// {row split, merge path, entry split}, vecs {1, 2, 4}; indices 9..23 are unused.
+GBSP_EXPORT int gbsp_sddmm_variant_opts(int variant, gbsp_opts *out) {
+    if (!out) return fail(GBSP_ERR_INVALID_ARG, "sddmm_variant_opts: null output");
+    if (variant < 0 || variant >= kSddmmVariants)
+        return fail(GBSP_ERR_INVALID_ARG, "sddmm_variant_opts: index %d outside 0..%d", variant, kSddmmVariants - 1);
+    static const int splits[3] = {GBSP_VARIANT_ROWSPLIT, GBSP_VARIANT_MERGE, GBSP_VARIANT_ENTRY};
+    static const int vecs[3] = {1, 2, 4};
+    *out = gbsp_opts{};
+    out->variant = splits[variant / 3];
+    out->vecs = vecs[variant % 3];
+    return ok();
+}
+
+GBSP_EXPORT int gbsp_autotune_sddmm(const gbsp_csr *S, const gbsp_dense *X, const gbsp_dense *Y, float *out, int reps,
+                                    float *times_ms, int32_t *best, void *stream) {
+    if (!S || !X || !Y || !out || !times_ms || reps < 1)
+        return fail(GBSP_ERR_INVALID_ARG, "autotune_sddmm: bad arguments");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return check_launch("autotune events");
+    int bi = -1;
+    int st = GBSP_OK;
+    for (int v = 0; v < kV && st == GBSP_OK; ++v) {
+        times_ms[v] = INFINITY;
+        if (v >= kSddmmVariants) continue;
+        gbsp_opts o;
+        gbsp_sddmm_variant_opts(v, &o);
+        float ms = 0.f;
+        if (!time_variant([&] { return sddmm_csr_ex(S, X, Y, out, &o, stream); }, reps, s, e0, e1, &ms, &st))
+            continue;
+        times_ms[v] = ms;
+        if (bi < 0 || times_ms[v] < times_ms[bi]) bi = v;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    if (best) *best = bi;
+    ok();
+    return bi < 0 ? fail(GBSP_ERR_UNSUPPORTED, "autotune_sddmm: no variant ran") : GBSP_OK;
 }

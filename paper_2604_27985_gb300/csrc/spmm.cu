@@ -11,6 +11,8 @@ int launch_spmm_typed(const SpmmProblem &P, int variant, int vecs, int unroll, i
         return check_launch("spmm scalar");
     }
     if (variant == GBSP_VARIANT_MERGE) return launch_spmm_algo<EL, GBSP_VARIANT_MERGE>(P, vecs, unroll, ctas_per_sm, s);
+    if (variant == GBSP_VARIANT_ROWGROUP)
+        return launch_spmm_algo<EL, GBSP_VARIANT_ROWGROUP>(P, vecs, unroll, ctas_per_sm, s);
     return launch_spmm_algo<EL, GBSP_VARIANT_ROWSPLIT>(P, vecs, unroll, ctas_per_sm, s);
 }
 

@@ -1,0 +1,6 @@
+// SpMM instantiation: E4M3 operands, row-group kernels.
+#include "spmm_launch.cuh"
+
+namespace gbsp {
+template int launch_spmm_algo<E4M3, GBSP_VARIANT_ROWGROUP>(const SpmmProblem &, int, int, int, cudaStream_t);
+}  // namespace gbsp

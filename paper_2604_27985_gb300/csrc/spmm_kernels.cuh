@@ -56,12 +56,7 @@ __device__ __forceinline__ void gather_step(const uint4 *__restrict__ Bv, int64_
 #pragma unroll
     for (int u = 0; u < U; ++u) {
 #pragma unroll
-        for (int v = 0; v < VPL; ++v) {
-            float f[EL::V];
-            EL::unpack(raw[u][v], f);
-#pragma unroll
-            for (int k = 0; k < EL::V; ++k) acc[v][k] = fmaf(aj[u], f[k], acc[v][k]);
-        }
+        for (int v = 0; v < VPL; ++v) EL::axpy(aj[u], raw[u][v], acc[v]);
     }
 }
 
@@ -100,15 +95,15 @@ __device__ __forceinline__ void gather_range(const SpmmProblem &P, int64_t p0, i
             for (int q = 0; q < 32; q += STEP)
                 gather_step<EL, LPN, VPL, U, CHECK_COLS, false>(Bv, ldv, c, a, q, 32, sub, colok, acc);
         } else {
-            // the row's last, partial chunk: whole steps unchecked, then one nonzero per group
+            // the row's last, partial chunk: whole steps unchecked, then the rest (fewer than
+            // STEP entries) in one predicated step, so its U gathers per lane are in flight
+            // together rather than one round trip each
             const int cnt = (int)(p1 - base);
             int q = 0;
 #pragma unroll 1
             for (; q + STEP <= cnt; q += STEP)
                 gather_step<EL, LPN, VPL, U, CHECK_COLS, false>(Bv, ldv, c, a, q, cnt, sub, colok, acc);
-#pragma unroll 1
-            for (; q < cnt; q += G)
-                gather_step<EL, LPN, VPL, 1, CHECK_COLS, true>(Bv, ldv, c, a, q, cnt, sub, colok, acc);
+            if (q < cnt) gather_step<EL, LPN, VPL, U, CHECK_COLS, true>(Bv, ldv, c, a, q, cnt, sub, colok, acc);
         }
         base = nb;
         c = c2;
@@ -247,6 +242,67 @@ __global__ void __launch_bounds__(256) spmm_merge_fixup_kernel(const SpmmProblem
             s += carry_val[((int64_t)blockIdx.y * nwarps + w2) * TW + col];
         float *dst = P.C + (int64_t)r * P.ldc + gcol;
         *dst += s * sc;
+    }
+}
+
+// Several consecutive rows per warp, one lane group of LPN lanes each (G = 32 / LPN rows
+// per warp): the plan-free form of the hyper-sparse treatment, for matrices whose rows hold
+// a few entries, where one warp per row leaves most of its groups idle.  Every lane of a
+// group gathers its VPL vectors of each entry's B row, U entries in flight; the group's
+// lanes load the same index and value (one broadcast) and no cross-group reduction is
+// needed.  A long row keeps its group busy alone, so this layout only suits short rows.
+template <class EL, int LPN, int VPL, int U>
+__global__ void __launch_bounds__(256) spmm_rowgroup_kernel(const SpmmProblem P) {
+    constexpr int G = 32 / LPN;
+    constexpr int TW = LPN * VPL * EL::V;
+    const int lane = threadIdx.x & 31;
+    const int64_t row = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * G + lane / LPN;
+    if (row >= P.M) return;  // a group's lanes share the row; no warp-wide exchange follows
+    const int col_base = blockIdx.y * TW + (lane % LPN) * EL::V;
+    const uint4 *Bv = static_cast<const uint4 *>(P.B) + col_base / EL::V;
+    const int64_t ldv = P.ldb / EL::V;
+    bool colok[VPL];
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) colok[v] = col_base + v * LPN * EL::V < P.N;
+    float acc[VPL][EL::V];
+#pragma unroll
+    for (int v = 0; v < VPL; ++v)
+#pragma unroll
+        for (int k = 0; k < EL::V; ++k) acc[v][k] = 0.f;
+    const int64_t p0 = __ldg(P.rowptr + row), p1 = __ldg(P.rowptr + row + 1);
+    for (int64_t p = p0; p < p1; p += U) {
+        int c[U];
+        float a[U];
+        bool ok[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            ok[u] = p + u < p1;
+            c[u] = ok[u] ? ld_stream(P.colidx + p + u) : 0;
+            a[u] = ok[u] ? coef<EL>(P, p + u, c[u]) : 0.f;
+        }
+        uint4 raw[U][VPL];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int v = 0; v < VPL; ++v)
+                raw[u][v] = (ok[u] && colok[v]) ? ld_gather16(Bv + (int64_t)c[u] * ldv + v * LPN)
+                                                : make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int v = 0; v < VPL; ++v) EL::axpy(a[u], raw[u][v], acc[v]);
+    }
+    const float sc = row_scale<EL>(P, (int)row);
+    float *dst = P.C + row * P.ldc;
+#pragma unroll
+    for (int v = 0; v < VPL; ++v) {
+        const int col = col_base + v * LPN * EL::V;
+        if (col < P.N) {
+#pragma unroll
+            for (int k = 0; k < EL::V; k += 4)
+                __stcs(reinterpret_cast<float4 *>(dst + col + k),
+                       make_float4(acc[v][k] * sc, acc[v][k + 1] * sc, acc[v][k + 2] * sc, acc[v][k + 3] * sc));
+        }
     }
 }
 

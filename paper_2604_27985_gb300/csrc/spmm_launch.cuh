@@ -38,6 +38,12 @@ int run(const SpmmProblem &P, int ctas_per_sm, cudaStream_t s) {
         scratch_free(cv, s);
         scratch_free(cr, s);
         return st;
+    } else if constexpr (ALGO == GBSP_VARIANT_ROWGROUP) {
+        constexpr int G = 32 / LPN;
+        const int64_t blocks = ((int64_t)P.M + 8 * G - 1) / (8 * G);
+        spmm_rowgroup_kernel<EL, LPN, VPL, U><<<dim3((unsigned)blocks, ntiles), 256, 0, s>>>(P);
+        count_launches(1);
+        return check_launch("spmm rowgroup");
     } else {
         spmm_rowsplit_kernel<EL, LPN, VPL, U><<<dim3((P.M + 7) / 8, ntiles), 256, 0, s>>>(P);
         count_launches(1);

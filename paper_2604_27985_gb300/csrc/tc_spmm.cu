@@ -266,11 +266,12 @@ __global__ void __launch_bounds__(kTcThreads) tc_window_kernel(const __grid_cons
                 const int col = q < kStagedCols ? s_cols[q] : a.blk_col[b0 + q];
                 const int y = col >= 0 ? col * kBC : a.K;  // padding block: rows past K read as zeros
                 if (a.block_box) {
-                    tma_load_3d(bt + kb * SH::NFA * 1024, &tmB, &full[s], 0, y, 0);
+                    tma_load_3d(bt + kb * SH::NFA * 1024, &tmB, &full[s], 0, y, (int)blockIdx.y * SH::NFA);
                 } else {
 #pragma unroll
                     for (int fa = 0; fa < SH::NFA; ++fa)
-                        tma_load_2d(bt + (kb * SH::NFA + fa) * 1024, &tmB, &full[s], (FP8 ? 128 : 64) * fa, y);
+                        tma_load_2d(bt + (kb * SH::NFA + fa) * 1024, &tmB, &full[s],
+                                    (FP8 ? 128 : 64) * ((int)blockIdx.y * SH::NFA + fa), y);
                 }
             }
             issued = ch + 1;
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(kTcThreads) tc_window_kernel(const __grid_cons
         for (int h = 0; h < NT; ++h) {
             float v[16];
             tmem_ld16(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)(h * 16), v);
-            const int f = 128 * h + 32 * warp + lane;
+            const int f = 128 * ((int)blockIdx.y * NT + h) + 32 * warp + lane;
             if (f < a.N) {
 #pragma unroll
                 for (int r = 0; r < kBR; ++r) {
@@ -801,6 +802,7 @@ struct gbsp_plan {
     int *err;
     int withhold;  // see gbsp_plan_test_withhold
     gbsp_opts residual_opts;
+    int residual_auto;  // the split AUTO chose for the residual at creation (0: not measured)
 };
 
 namespace {
@@ -858,7 +860,7 @@ EncodeTiledFn encode_fn() {
 }
 
 template <int NT, bool FP8>
-int launch_tc(const CUtensorMap &map, const TcArgs &args, int nwin, cudaStream_t s) {
+int launch_tc(const CUtensorMap &map, const TcArgs &args, int nwin, int ngroups, cudaStream_t s) {
     using SH = TcShape<NT, FP8>;
     static bool attr_set[64] = {false};
     int dev = 0;
@@ -870,7 +872,7 @@ int launch_tc(const CUtensorMap &map, const TcArgs &args, int nwin, cudaStream_t
             return check_launch("tc smem attribute");
         attr_set[dev] = true;
     }
-    tc_window_kernel<NT, FP8><<<nwin, kTcThreads, SH::SMEM, s>>>(map, args);
+    tc_window_kernel<NT, FP8><<<dim3((unsigned)nwin, (unsigned)ngroups), kTcThreads, SH::SMEM, s>>>(map, args);
     count_launches(1);
     return check_launch("tc window kernel");
 }
@@ -1007,6 +1009,13 @@ GBSP_EXPORT int gbsp_plan_create(const gbsp_csr *A, int32_t threshold, const gbs
         GBSP_TRY(check_launch("plan residual"));
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) GBSP_TRY(check_launch("plan sync"));
+    if (p->residual_opts.variant == GBSP_VARIANT_AUTO && M > 0) {
+        // the residual's automatic split is measured here, where the stream is synchronised
+        // anyway, so that executions never synchronise
+        const gbsp_csr R{p->M, p->K, p->res_nnz, p->res_rowptr, p->res_colidx, p->res_vals, p->res_scale, p->dtype};
+        // (the B of later executions is not known yet: the rule is applied as for B in L2)
+        GBSP_TRY(auto_choice(R, kOpSpmm, 0, 0, s, &p->residual_auto, nullptr));
+    }
 out:
 #undef GBSP_TRY
     cudaFree(slot);
@@ -1039,9 +1048,10 @@ int encode_b_map(const gbsp_dense *B, int64_t K, bool fp8, int nt, CUtensorMap *
     *block_box = 0;
     if (N % 128 == 0) {
         const int natoms = (int)(N / atom);
+        const int tile_atoms = fp8 ? 1 : 2;  // atoms of one 128-feature tile, gathered per CTA
         const cuuint64_t dims3[3] = {(cuuint64_t)atom, (cuuint64_t)K, (cuuint64_t)natoms};
         const cuuint64_t strides3[2] = {(cuuint64_t)B->ld * es, 128};
-        const cuuint32_t box3[3] = {(cuuint32_t)atom, 8, (cuuint32_t)natoms};
+        const cuuint32_t box3[3] = {(cuuint32_t)atom, 8, (cuuint32_t)tile_atoms};
         const cuuint32_t estr3[3] = {1, 1, 1};
         *block_box = natoms == (fp8 ? nt : 2 * nt) &&
                      enc(map, ty, 3, B->data, dims3, strides3, box3, estr3, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -1061,14 +1071,14 @@ int encode_b_map(const gbsp_dense *B, int64_t K, bool fp8, int nt, CUtensorMap *
     return GBSP_OK;
 }
 
+// One CTA per dense window and 128-feature tile: a window's tiles read the same value
+// tiles but gather disjoint atoms of each B row and write disjoint columns of C, so
+// splitting them doubles (N = 256) or quadruples (N = 512) the work items without any
+// combining step; with one item per window the 1,024 windows of a 16,384-row matrix fill
+// 1.35 waves of 5 CTAs per SM and leave most of the second wave's slots idle.
 template <bool FP8>
 int launch_tc_nt(int nt, const CUtensorMap &map, const TcArgs &args, int nwin, cudaStream_t s) {
-    switch (nt) {
-        case 1: return launch_tc<1, FP8>(map, args, nwin, s);
-        case 2: return launch_tc<2, FP8>(map, args, nwin, s);
-        case 3: return launch_tc<3, FP8>(map, args, nwin, s);
-        default: return launch_tc<4, FP8>(map, args, nwin, s);
-    }
+    return launch_tc<1, FP8>(map, args, nwin, nt, s);
 }
 
 }  // namespace
@@ -1091,7 +1101,10 @@ GBSP_EXPORT int gbsp_plan_execute(const gbsp_plan *p, const gbsp_dense *B, gbsp_
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // residual entries (and the overwrite of C) through the CSR kernels
     gbsp_csr R{p->M, p->K, p->res_nnz, p->res_rowptr, p->res_colidx, p->res_vals, p->res_scale, p->dtype};
-    int st = spmm_csr_ex(&R, B, C, &p->residual_opts, stream);
+    gbsp_opts ro = p->residual_opts;
+    const bool vec = aligned16(B->data) && B->ld % amul == 0 && N % amul == 0 && aligned16(C->data) && C->ld % 4 == 0;
+    if (ro.variant == GBSP_VARIANT_AUTO && p->residual_auto > 0 && vec) ro.variant = p->residual_auto;
+    int st = spmm_csr_ex(&R, B, C, &ro, stream);
     if (st) return st;
     if (p->nwin_tc == 0 || N == 0) return ok();
     const int nt = (int)((N + 127) / 128);

@@ -108,6 +108,27 @@ def sddmm(rowptr, colidx, svals, X, Y, out=None, *, x_scale=None, y_scale=None, 
     return out
 
 
+def auto_choice(rowptr, ncols, colidx=None, op="spmm", b_bytes=0, row_bytes=0, stream=None) -> tuple[str, dict]:
+    """The split GBSP_VARIANT_AUTO takes on this pattern for op "spmm" ('rowsplit', 'merge'
+    or 'rowgroup') or "sddmm" ('rowsplit', 'merge' or 'entry'), with a gathered dense operand
+    of b_bytes bytes in rows of row_bytes (0: unknown), and the row statistics it was chosen
+    from (gbsp_auto_choice; a new pattern is measured at once, synchronising the stream)."""
+    A = Csr(rowptr.numel() - 1, int(ncols), -1, _ptr(rowptr), _ptr(colidx) if colidx is not None else None, None,
+            None, F32)
+    v = ctypes.c_int32(0)
+    st = (ctypes.c_int64 * 5)()
+    check(lib.gbsp_auto_choice(ctypes.byref(A), {"spmm": 0, "sddmm": 1}[op], int(b_bytes), int(row_bytes),
+                               _stream(stream), ctypes.byref(v), st))
+    names = {k: n for n, k in VARIANTS.items()}
+    keys = ("rows", "nnz", "sum_sq_lengths", "max_length", "empty_rows")
+    return names[v.value], dict(zip(keys, list(st)))
+
+
+def auto_forget() -> None:
+    """Drops every choice GBSP_VARIANT_AUTO has kept."""
+    lib.gbsp_auto_forget()
+
+
 def csr_validate(rowptr, colidx, ncols, stream=None) -> int:
     """Number of CSR violations (0 for a valid matrix); synchronises the stream."""
     A = Csr(rowptr.numel() - 1, int(ncols), colidx.numel(), _ptr(rowptr), _ptr(colidx), _ptr(colidx) or 1,
@@ -247,6 +268,43 @@ class KbinPlan:
             pass
 
 
+class SellPlan:
+    """SELL-C-sigma SpMM plan of an FP32 CSR matrix (gbsp_sell_plan_create): rows sorted by
+    length within windows of sigma rows, slices of C rows padded and stored column-major, one
+    lane group per row.  ``execute(B)`` returns C = A B.  The plan owns its copy of A."""
+
+    def __init__(self, rowptr, colidx, vals, ncols, C=0, sigma=0, stream=None):
+        self.M = rowptr.numel() - 1
+        self.K = int(ncols)
+        A = _csr(rowptr, colidx, vals, ncols)
+        h = ctypes.c_void_p()
+        check(lib.gbsp_sell_plan_create(ctypes.byref(A), int(C), int(sigma), _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    def execute(self, B, out=None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.M, B.shape[1]), dtype=torch.float32, device=B.device)
+        b, c = _dense(B), _dense(out)
+        check(lib.gbsp_sell_plan_execute(self._h, ctypes.byref(b), ctypes.byref(c), _stream(stream)))
+        return out
+
+    def info(self) -> dict:
+        arr = (ctypes.c_int64 * 5)()
+        check(lib.gbsp_sell_plan_info(self._h, arr, 5))
+        return {"slices": arr[0], "C": arr[1], "sigma": arr[2], "slots": arr[3], "nnz": arr[4]}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib.gbsp_sell_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class HspPlan:
     """Hyper-sparse SpMM plan of an FP32 CSR matrix (gbsp_hsp_plan_create): rows binned by
     length (long rows one warp each, short rows one lane group each, empty rows zeroed) in
@@ -353,12 +411,27 @@ N_FEATURES = 16
 N_PARAMS = 16 * 64 + 64 + 64 * 64 + 64 + 24 * 64 + 24
 
 
+N_SDDMM_VARIANTS = 9
+HSP_PLAN = "hsp_plan"
+
+
 def variant_options(v: int) -> dict:
-    """spmm keyword arguments of selector variant v (gbsp_variant_opts)."""
+    """spmm keyword arguments of selector variant v (gbsp_variant_opts); variant 23, the
+    hyper-sparse plan, comes back as {"variant": "hsp_plan"} (build an HspPlan and execute
+    it instead of calling spmm)."""
     o = Opts()
     check(lib.gbsp_variant_opts(int(v), ctypes.byref(o)))
-    name = {1: "rowsplit", 2: "merge", 3: "scalar"}[o.variant]
+    if o.variant == 6:
+        return {"variant": HSP_PLAN}
+    name = {1: "rowsplit", 2: "merge", 3: "scalar", 5: "rowgroup"}[o.variant]
     return {"variant": name, "vecs": o.vecs, "unroll": o.unroll, "ctas_per_sm": o.ctas_per_sm}
+
+
+def sddmm_variant_options(v: int) -> dict:
+    """sddmm keyword arguments of SDDMM selector variant v (gbsp_sddmm_variant_opts)."""
+    o = Opts()
+    check(lib.gbsp_sddmm_variant_opts(int(v), ctypes.byref(o)))
+    return {"variant": {1: "rowsplit", 2: "merge", 4: "entry"}[o.variant], "vecs": o.vecs}
 
 
 def features(rowptr, colidx, ncols, N, dtype=F32, out=None, stream=None) -> torch.Tensor:
@@ -397,6 +470,17 @@ def autotune(rowptr, colidx, vals, B, C, reps=3, a_scale=None, b_scale=None, str
     best = ctypes.c_int32(-1)
     check(lib.gbsp_autotune(ctypes.byref(A), ctypes.byref(b), ctypes.byref(c), int(reps), times, ctypes.byref(best),
                             _stream(stream)))
+    return [times[i] for i in range(N_VARIANTS)], best.value
+
+
+def autotune_sddmm(rowptr, colidx, svals, X, Y, out, reps=3, x_scale=None, y_scale=None, stream=None):
+    """Times of the SDDMM variants (ms; inf at 9..23 and where not applicable) and the best."""
+    S = _csr(rowptr, colidx, svals, Y.shape[0])
+    x, y = _dense(X, x_scale), _dense(Y, y_scale)
+    times = (ctypes.c_float * N_VARIANTS)()
+    best = ctypes.c_int32(-1)
+    check(lib.gbsp_autotune_sddmm(ctypes.byref(S), ctypes.byref(x), ctypes.byref(y), _ptr(out), int(reps), times,
+                                  ctypes.byref(best), _stream(stream)))
     return [times[i] for i in range(N_VARIANTS)], best.value
 
 

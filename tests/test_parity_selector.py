@@ -111,8 +111,115 @@ def test_autotune_bookkeeping(gb):
     ref, sc = oracle.spmm(A.rowptr, A.colidx, A.vals, B)
     from _util import assert_within
 
-    assert_within(C.cpu().numpy(), ref, sc, 1e-5, "last autotuned variant")
-    for v in (0, 9, 18, 22, 23):
+    assert_within(C.cpu().numpy(), ref, sc, 1e-5, "last autotuned variant (the hyper-sparse plan)")
+    for v in (0, 9, 18, 22):
         kw = gb.variant_options(v)
         out = gb.spmm(dev(A.rowptr), dev(A.colidx), dev(A.vals), dev(B), **kw).cpu().numpy()
         assert_within(out, ref, sc, 1e-5, f"variant {v}")
+    assert gb.variant_options(22)["variant"] == "rowgroup" and gb.variant_options(23) == {"variant": "hsp_plan"}
+    # BF16: the hyper-sparse plan (FP32 only) does not apply
+    times16, best16 = gb.autotune(dev(A.rowptr), dev(A.colidx), gb.quantize_bf16(dev(A.vals)),
+                                  gb.quantize_bf16(dev(B)), C, reps=1)
+    assert np.isinf(times16[23]) and all(np.isfinite(times16[:23])) and best16 == int(np.argmin(times16))
+
+
+def test_autotune_sddmm_bookkeeping(gb):
+    import torch
+
+    A = gen.csr_powerlaw(4000, 3000, 0.99, seed=612)
+    X, Y = gen.dense_normal(A.M, 64, 613), gen.dense_normal(A.K, 64, 614)
+    out = torch.empty(A.nnz, device="cuda")
+    times, best = gb.autotune_sddmm(dev(A.rowptr), dev(A.colidx), dev(A.vals), dev(X), dev(Y), out, reps=2)
+    assert len(times) == 24 and all(np.isfinite(times[:9])) and all(np.isinf(times[9:]))
+    assert best == int(np.argmin(times))
+    ref, sc = oracle.sddmm(A.rowptr, A.colidx, A.vals, X, Y)
+    from _util import assert_within
+
+    assert_within(out.cpu().numpy(), ref, sc, 1e-5, "last autotuned SDDMM variant")
+    for v in range(gb.N_SDDMM_VARIANTS):
+        o = gb.sddmm(dev(A.rowptr), dev(A.colidx), dev(A.vals), dev(X), dev(Y),
+                     **gb.sddmm_variant_options(v)).cpu().numpy()
+        assert_within(o, ref, sc, 1e-5, f"sddmm variant {v}")
+
+
+def _untrained(op, **kw):
+    from paper_2604_27985_gb300 import selector as sel
+
+    s = sel.Selector(seed=3, op=op, **kw)
+    rng = np.random.default_rng(615)
+    s.norm = dev(np.r_[rng.standard_normal(16), np.ones(16)].astype(np.float32))
+    return s
+
+
+def test_selector_fallback_outside_training_range(gb):
+    """A matrix whose features lie outside the training range goes to the autotuner; its
+    best is kept per pattern (the second call does not autotune again) and the result is the
+    oracle's."""
+    from _util import assert_within
+
+    s = _untrained("spmm", margin=0.0, gap=0.0)
+    s.fmin, s.fmax = np.full(16, -1e-3), np.full(16, 1e-3)  # nothing real fits
+    A = gen.csr_powerlaw(3000, 3000, 0.995, seed=616)
+    B = gen.dense_normal(A.K, 64, 617)
+    rp, ci, v, Bd = dev(A.rowptr), dev(A.colidx), dev(A.vals), dev(B)
+    choice, reason = s.decide(rp, ci, A.K, 64, tune=lambda: gb.autotune(rp, ci, v, Bd,
+                                                                          gb.spmm(rp, ci, v, Bd))[1])
+    assert reason == "range" and 0 <= choice < 24
+    ref, sc = oracle.spmm(A.rowptr, A.colidx, A.vals, B)
+    for _ in range(2):
+        C = s.spmm(rp, ci, v, Bd).cpu().numpy()
+        assert_within(C, ref, sc, 1e-5, "fallback choice")
+    assert s.counts["autotuned"] == 1 and s.counts["range"] == 3
+
+
+def test_selector_fallback_when_top_two_are_close(gb):
+    from _util import assert_within
+
+    s = _untrained("spmm", margin=1e9, gap=1e9)  # every prediction counts as ambiguous
+    s.fmin, s.fmax = np.zeros(16), np.ones(16)
+    A = gen.csr_uniform(4000, 4000, 0.999, seed=618)
+    B = gen.dense_normal(A.K, 32, 619)
+    rp, ci, v, Bd = dev(A.rowptr), dev(A.colidx), dev(A.vals), dev(B)
+    v_sel = s.choose(rp, ci, A.K, 32)
+    assert s.counts["gap"] == 1 and s.counts["autotuned"] == 1
+    C = s.run_spmm(v_sel, rp, ci, v, Bd, gb.spmm(rp, ci, v, Bd)).cpu().numpy()
+    ref, sc = oracle.spmm(A.rowptr, A.colidx, A.vals, B)
+    assert_within(C, ref, sc, 1e-5, "gap fallback choice")
+    # without the fallback the model's own choice stands (over the applicable variants)
+    s2 = _untrained("spmm", margin=1e9, gap=0.0)
+    s2.fmin, s2.fmax = np.zeros(16), np.ones(16)
+    f = gb.features(rp, ci, A.K, 32)
+    out, _ = gb.mlp_predict(s2.weights, s2.norm, f.reshape(1, -1))
+    assert s2.choose(rp, ci, A.K, 32) == int(np.argmin(out.cpu().numpy()[0]))
+    assert s2.counts["autotuned"] == 0
+
+
+def test_selector_runs_the_hyper_sparse_plan_variant(gb):
+    from _util import assert_within
+
+    s = _untrained("spmm")
+    A = gen.csr_uniform(20000, 20000, 0.9999, seed=620)
+    B = gen.dense_normal(A.K, 64, 621)
+    rp, ci, v, Bd = dev(A.rowptr), dev(A.colidx), dev(A.vals), dev(B)
+    ref, sc = oracle.spmm(A.rowptr, A.colidx, A.vals, B)
+    for _ in range(2):  # built once, then reused
+        C = s.run_spmm(23, rp, ci, v, Bd, gb.spmm(rp, ci, v, Bd)).cpu().numpy()
+        assert_within(C, ref, sc, 1e-5, "hyper-sparse plan through the selector")
+    assert len(s._plans) == 1
+
+
+def test_sddmm_selector_with_fallback(gb):
+    from _util import assert_within
+
+    s = _untrained("sddmm", margin=0.0, gap=0.0)
+    s.fmin, s.fmax = np.full(16, -1e-3), np.full(16, 1e-3)
+    A = gen.csr_powerlaw(3000, 3000, 0.99, seed=622)
+    X, Y = gen.dense_normal(A.M, 128, 623), gen.dense_normal(A.K, 128, 624)
+    rp, ci, v = dev(A.rowptr), dev(A.colidx), dev(A.vals)
+    out = s.sddmm(rp, ci, v, dev(X), dev(Y)).cpu().numpy()
+    assert s.counts["range"] == 1 and s.counts["autotuned"] == 1
+    ref, sc = oracle.sddmm(A.rowptr, A.colidx, A.vals, X, Y)
+    assert_within(out, ref, sc, 1e-5, "sddmm selector")
+    # the model alone picks among the 9 SDDMM variants only
+    s2 = _untrained("sddmm", margin=1e9, gap=0.0)
+    assert 0 <= s2.choose(rp, ci, A.K, 128) < gb.N_SDDMM_VARIANTS
