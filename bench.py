@@ -195,7 +195,8 @@ def kernel_traffic():
 
 TRAFFIC_SOURCES = ["paper_2604_27985_gb300/csrc/common.cuh", "paper_2604_27985_gb300/csrc/spmm_kernels.cuh",
                    "paper_2604_27985_gb300/csrc/spmm_launch.cuh", "paper_2604_27985_gb300/csrc/sddmm_kernels.cuh",
-                   "paper_2604_27985_gb300/csrc/sddmm.cu", "paper_2604_27985_gb300/csrc/api.cu"]
+                   "paper_2604_27985_gb300/csrc/sddmm.cu", "paper_2604_27985_gb300/csrc/api.cu",
+                   "paper_2604_27985_gb300/csrc/auto.cu"]
 
 
 def sources_sha256(names):
@@ -206,21 +207,21 @@ def sources_sha256(names):
     return h.hexdigest()
 
 
-def write_traffic(report, spmm_re, sddmm_re):
+def write_traffic(spmm_report, spmm_re, sddmm_report, sddmm_re):
     """Stores per-launch DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the
-    SpMM and SDDMM kernels from an ncu report in profiles/traffic.json, stamped with the
-    sha256 of the kernel sources: bench lines carry them only while the kernels are
-    unchanged."""
+    SpMM and SDDMM kernels from ncu reports (one report may hold both) in
+    profiles/traffic.json, stamped with the sha256 of the kernel sources: bench lines carry
+    them only while the kernels are unchanged."""
     import csv
     import io
     import re
 
-    out = subprocess.run(["ncu", "-i", report, "--page", "raw", "--csv"], capture_output=True, text=True).stdout
-    rows = list(csv.reader(io.StringIO(out)))
-    hdr, units = rows[0], rows[1]
     scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
 
-    def per_launch(pattern):
+    def per_launch(report, pattern):
+        out = subprocess.run(["ncu", "-i", report, "--page", "raw", "--csv"], capture_output=True, text=True).stdout
+        rows = list(csv.reader(io.StringIO(out)))
+        hdr, units = rows[0], rows[1]
         vals = []
         for r in rows[2:]:
             d = dict(zip(hdr, r))
@@ -229,9 +230,10 @@ def write_traffic(report, spmm_re, sddmm_re):
                                 for m in ("dram__bytes_read.sum", "dram__bytes_write.sum")))
         return sum(vals) / len(vals) if vals else None
 
-    t = {"report": os.path.basename(report), "sources": TRAFFIC_SOURCES,
+    t = {"reports": [os.path.basename(spmm_report), os.path.basename(sddmm_report)], "sources": TRAFFIC_SOURCES,
          "sources_sha256": sources_sha256(TRAFFIC_SOURCES),
-         "spmm_bytes_per_launch": per_launch(spmm_re), "sddmm_bytes_per_launch": per_launch(sddmm_re)}
+         "spmm_bytes_per_launch": per_launch(spmm_report, spmm_re),
+         "sddmm_bytes_per_launch": per_launch(sddmm_report, sddmm_re)}
     with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
         json.dump(t, f, indent=1)
     print(json.dumps(t))
@@ -1138,8 +1140,8 @@ def main():
     ap.add_argument("--selector-extrapolate", type=int, default=24)
     ap.add_argument("--selector-margin", type=float, default=0.1)
     ap.add_argument("--selector-gap", type=float, default=0.02)
-    ap.add_argument("--write-traffic", nargs=3, metavar=("REPORT", "SPMM_RE", "SDDMM_RE"),
-                    help="store per-launch DRAM bytes from an ncu report and exit")
+    ap.add_argument("--write-traffic", nargs=4, metavar=("SPMM_REPORT", "SPMM_RE", "SDDMM_REPORT", "SDDMM_RE"),
+                    help="store per-launch DRAM bytes from ncu reports and exit")
     args = ap.parse_args()
     if args.write_traffic:
         write_traffic(*args.write_traffic)

@@ -67,7 +67,9 @@ typedef enum {
                                   rows (short or skewed rows); GBSP_ERR_UNSUPPORTED for SpMM */
     GBSP_VARIANT_ROWGROUP = 5, /* SpMM only: several consecutive rows per warp, one lane group each
                                   (rows of a few entries); GBSP_ERR_UNSUPPORTED for SDDMM */
-    GBSP_VARIANT_HSP_PLAN = 6  /* a selector label only: the hyper-sparse plan (gbsp_hsp_plan_*);
+    GBSP_VARIANT_HSP_PLAN = 6, /* a selector label only: the hyper-sparse plan (gbsp_hsp_plan_*);
+                                  spmm_csr_ex returns GBSP_ERR_UNSUPPORTED for it */
+    GBSP_VARIANT_SELL_PLAN = 7 /* a selector label only: the SELL-C-sigma plan (gbsp_sell_plan_*);
                                   spmm_csr_ex returns GBSP_ERR_UNSUPPORTED for it */
 } gbsp_variant;
 
@@ -142,7 +144,8 @@ int spmm_csr_ex(const gbsp_csr *A, const gbsp_dense *B, gbsp_dense *C, const gbs
  * out is float[S->nnz] in CSR order.  X->rows = S->rows, Y->rows = S->cols,
  * X->cols = Y->cols = Kd.  GBSP_VARIANT_AUTO takes the entry split when rows average under 32
  * stored entries, the merge path on skewed rows (coefficient of variation above 1, or a
- * longest row past 16 times the mean and past 256) and the row split otherwise, from the
+ * longest row past 16 times the mean and past 256) and on even rows gathered from a Y of more
+ * than 192 MB in rows of at least 256 bytes, and the row split otherwise, from the
  * same kept row statistics as spmm_csr_ex's AUTO (measured, kept and re-measured as
  * described there); unvectorisable operands take the scalar kernel. */
 int sddmm_csr_ex(const gbsp_csr *S, const gbsp_dense *X, const gbsp_dense *Y, float *out,
@@ -398,7 +401,9 @@ void gbsp_sell_plan_destroy(gbsp_sell_plan *plan);
 /* The 24 SpMM variants the selector chooses among, as options for spmm_csr_ex:
  *   0..8   row-split, vecs {1,2,4} x unroll {2,4,8}     (index = 3 * vecs_index + unroll_index)
  *   9..17  merge path, the same nine layouts
- *   18..21 merge path with 1 or 2 CTAs per SM, vecs {1,2}, unroll 4
+ *   18..20 merge path with 1 CTA per SM and vecs {1,2}, or 2 CTAs per SM and vecs 1; unroll 4
+ *   21     the SELL-C-sigma plan: out->variant = GBSP_VARIANT_SELL_PLAN, meaning "create a
+ *          gbsp_sell_plan of A once (C = 64, one sort window) and execute it" (FP32 only)
  *   22     row groups (GBSP_VARIANT_ROWGROUP), default layout
  *   23     the hyper-sparse plan: out->variant = GBSP_VARIANT_HSP_PLAN, meaning "create a
  *          gbsp_hsp_plan of A once and execute it" (FP32 only); not an spmm_csr_ex option. */
@@ -437,8 +442,8 @@ int gbsp_mlp_train(float *weights, float *adam, const float *norm, const float *
                    void *stream);
 
 /* Times every SpMM variant of gbsp_variant_opts on A, B, C (one untimed call, then reps
- * timed calls with CUDA events; variant 23 builds a hyper-sparse plan of A first, outside
- * the timed calls, so A->nnz must be given) and writes times_ms[24] (host; INFINITY where a
+ * timed calls with CUDA events; variants 21 and 23 build a SELL-C-sigma or hyper-sparse
+ * plan of A first, outside the timed calls, so A->nnz must be given) and writes times_ms[24] (host; INFINITY where a
  * variant does not apply) and *best (host).  Synchronises the stream; C ends up holding the
  * last variant's result. */
 int gbsp_autotune(const gbsp_csr *A, const gbsp_dense *B, gbsp_dense *C, int reps, float *times_ms,

@@ -188,8 +188,9 @@ GBSP_EXPORT int spmm_csr_ex(const gbsp_csr *A, const gbsp_dense *B, gbsp_dense *
                                     "multiples of %d", elems_per_vec(B->dtype));
     if (variant == GBSP_VARIANT_ENTRY)
         return fail(GBSP_ERR_UNSUPPORTED, "spmm: the entry split is an SDDMM variant (SpMM rows need one owner)");
-    if (variant == GBSP_VARIANT_HSP_PLAN)
-        return fail(GBSP_ERR_UNSUPPORTED, "spmm: the hyper-sparse plan runs through gbsp_hsp_plan_execute");
+    if (variant == GBSP_VARIANT_HSP_PLAN || variant == GBSP_VARIANT_SELL_PLAN)
+        return fail(GBSP_ERR_UNSUPPORTED, "spmm: the hyper-sparse and SELL-C-sigma plans run through their own "
+                                          "plan entry points");
     if (variant < GBSP_VARIANT_ROWSPLIT || variant > GBSP_VARIANT_ROWGROUP)
         return fail(GBSP_ERR_INVALID_ARG, "spmm: unknown variant %d", variant);
     SpmmProblem p{};
@@ -244,8 +245,8 @@ GBSP_EXPORT int sddmm_csr_ex(const gbsp_csr *S, const gbsp_dense *X, const gbsp_
     if (variant != GBSP_VARIANT_SCALAR && !vec)
         return fail(GBSP_ERR_ALIGN, "sddmm: vectorised variant needs 16-byte aligned X and Y, Kd and ld "
                                     "multiples of %d and Kd <= %d", V, 32 * 16);
-    if (variant == GBSP_VARIANT_ROWGROUP || variant == GBSP_VARIANT_HSP_PLAN)
-        return fail(GBSP_ERR_UNSUPPORTED, "sddmm: the row groups and the hyper-sparse plan are SpMM variants");
+    if (variant == GBSP_VARIANT_ROWGROUP || variant == GBSP_VARIANT_HSP_PLAN || variant == GBSP_VARIANT_SELL_PLAN)
+        return fail(GBSP_ERR_UNSUPPORTED, "sddmm: the row groups and the SpMM plans are SpMM variants");
     if (variant < GBSP_VARIANT_ROWSPLIT || variant > GBSP_VARIANT_ENTRY)
         return fail(GBSP_ERR_INVALID_ARG, "sddmm: unknown variant %d", variant);
     SddmmProblem p{};

@@ -144,22 +144,11 @@ struct E4M3 {
         return __half2float(*reinterpret_cast<__half *>(&h));
     }
     __device__ __forceinline__ static float scalar(const stored *p) { return value(*p); }
-    // acc[k] += a * element k of r: the codes decode in pairs (one conversion per two) and
-    // the products go through packed FP32 fmas (two single-rounding fmas per instruction,
-    // each exactly fmaf), which halves the FMA instructions of this ALU-bound form.
     __device__ __forceinline__ static void axpy(float a, const uint4 &r, float (&acc)[16]) {
-        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
-        const float2 aa = make_float2(a, a);
+        float o[16];
+        unpack(r, o);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float2 lo = pair((uint16_t)(w[i] & 0xffffu)), hi = pair((uint16_t)(w[i] >> 16));
-            const float2 r0 = __ffma2_rn(aa, lo, make_float2(acc[4 * i], acc[4 * i + 1]));
-            const float2 r1 = __ffma2_rn(aa, hi, make_float2(acc[4 * i + 2], acc[4 * i + 3]));
-            acc[4 * i] = r0.x;
-            acc[4 * i + 1] = r0.y;
-            acc[4 * i + 2] = r1.x;
-            acc[4 * i + 3] = r1.y;
-        }
+        for (int k = 0; k < 16; ++k) acc[k] = fmaf(a, o[k], acc[k]);
     }
     __device__ __forceinline__ static float dot(const uint4 &, const float (&xf)[16], const uint4 &yr, float sum) {
         float y[16];
@@ -199,6 +188,15 @@ __device__ __forceinline__ void dot2(const float (&x)[V], const float (&y)[V], f
 #pragma unroll
     for (int k = 0; k < V; k += 2) acc = __ffma2_rn(make_float2(x[k], x[k + 1]), make_float2(y[k], y[k + 1]), acc);
 }
+
+// Two adjacent 16-byte vectors of a gathered row with one 32-byte load (read-only path, L1
+// cached like ld_gather16); p must be 32-byte aligned.
+__device__ __forceinline__ void ld_gather32(const void *p, uint4 &a, uint4 &b) {
+    asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+                 : "l"(p));
+}
+inline bool aligned32(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 31u) == 0; }
 
 // Gathered dense rows: read-only path, 16 bytes per lane.  (Skipping L1 allocation for
 // them measured 1-9% slower on the 65,536^2 and 16,384^2 workloads, so they stay cached.)
@@ -276,7 +274,7 @@ constexpr int kOpSpmm = 0, kOpSddmm = 1;
 int auto_choice(const gbsp_csr &A, int op, int64_t b_bytes, int64_t row_bytes, cudaStream_t s, int *variant,
                 int64_t *stats);
 int auto_spmm_rule(int64_t M, int64_t nnz, int64_t sumsq, int64_t maxlen, int64_t b_bytes, int64_t row_bytes);
-int auto_sddmm_rule(int64_t M, int64_t nnz, int64_t sumsq, int64_t maxlen);
+int auto_sddmm_rule(int64_t M, int64_t nnz, int64_t sumsq, int64_t maxlen, int64_t y_bytes, int64_t row_bytes);
 void auto_forget_all();
 int launch_quant_bf16(const float *x, uint16_t *out, int64_t n, cudaStream_t s);
 int launch_quant_e4m3_rows(const float *x, const int32_t *rowptr, int64_t nrows, int64_t ncols,

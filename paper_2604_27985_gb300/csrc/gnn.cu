@@ -81,7 +81,7 @@ __device__ __forceinline__ void gnn_step(const uint4 *Hv, int64_t ldv, const boo
 #pragma unroll
         for (int off = LPN / 2; off >= 1; off >>= 1) dot += __shfl_xor_sync(FULL, dot, off);
         const float e = sj[u] * dot;
-        if (sl == 0 && ok[u]) E[base + q + u * G + sub] = e;
+        if (sl == 0 && ok[u]) __stcs(E + base + q + u * G + sub, e);  // written once: evict first, keep H in L2
 #pragma unroll
         for (int v = 0; v < VPL; ++v) axpy2(e, f[v], acc[v]);
     }
@@ -266,8 +266,8 @@ __device__ __forceinline__ void gnn_tile(const GraphDesc &g, int r0, int r1, int
             // lane reads back what it stored)
             const int64_t last = p1 > p0 ? p0 + ((p1 - p0 - 1) & ~(int64_t)31) : p0;  // the last chunk's start
             int64_t p = p0 + lane;
-            for (; p < last; p += 32) g.E[p] = exp2f(g.E[p] - row_max) * inv_sum;
-            if (p < p1) g.E[p] = exp2f(mine - row_max) * inv_sum;
+            for (; p < last; p += 32) __stcs(g.E + p, exp2f(g.E[p] - row_max) * inv_sum);
+            if (p < p1) __stcs(g.E + p, exp2f(mine - row_max) * inv_sum);
         }
         if (lane < LPN) {
 #pragma unroll
@@ -279,7 +279,8 @@ __device__ __forceinline__ void gnn_tile(const GraphDesc &g, int r0, int r1, int
                     __nv_bfloat162 h = __floats2bfloat162_rn(acc[v][2 * t], acc[v][2 * t + 1]);
                     w[t] = *reinterpret_cast<uint32_t *>(&h);
                 }
-                reinterpret_cast<uint4 *>(g.O + (int64_t)row * g.ldo)[v * LPN + sl] = make_uint4(w[0], w[1], w[2], w[3]);
+                __stcs(reinterpret_cast<uint4 *>(g.O + (int64_t)row * g.ldo) + v * LPN + sl,
+                       make_uint4(w[0], w[1], w[2], w[3]));  // written once: evict first, keep H in L2
             }
         }
         p0 = p1;

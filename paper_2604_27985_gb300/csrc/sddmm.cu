@@ -4,7 +4,7 @@
 namespace gbsp {
 namespace sddmm_detail {
 
-template <class EL, int LPN, int VPL>
+template <class EL, int LPN, int VPL, bool PAIR = false>
 int run(const SddmmProblem &P, int variant, cudaStream_t s) {
     if (variant == GBSP_VARIANT_ENTRY) {
         int per_sm = 0;
@@ -18,18 +18,18 @@ int run(const SddmmProblem &P, int variant, cudaStream_t s) {
     }
     if (variant == GBSP_VARIANT_MERGE) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sddmm_merge_kernel<EL, LPN, VPL>, 256, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sddmm_merge_kernel<EL, LPN, VPL, PAIR>, 256, 0) !=
             cudaSuccess)
             return check_launch("occupancy query");
         const int nblocks = sm_count() * (per_sm < 1 ? 1 : per_sm);
-        sddmm_merge_kernel<EL, LPN, VPL><<<dim3(nblocks), 256, 0, s>>>(P, nblocks * 8);
+        sddmm_merge_kernel<EL, LPN, VPL, PAIR><<<dim3(nblocks), 256, 0, s>>>(P, nblocks * 8);
         count_launches(1);
         return check_launch("sddmm merge");
     }
     if (P.pos)  // a plan's residual: values and outputs at the entries' original positions
-        sddmm_rowsplit_kernel<EL, LPN, VPL, true><<<dim3((P.M + 7) / 8), 256, 0, s>>>(P);
+        sddmm_rowsplit_kernel<EL, LPN, VPL, true, PAIR><<<dim3((P.M + 7) / 8), 256, 0, s>>>(P);
     else
-        sddmm_rowsplit_kernel<EL, LPN, VPL><<<dim3((P.M + 7) / 8), 256, 0, s>>>(P);
+        sddmm_rowsplit_kernel<EL, LPN, VPL, false, PAIR><<<dim3((P.M + 7) / 8), 256, 0, s>>>(P);
     count_launches(1);
     return check_launch("sddmm rowsplit");
 }
@@ -64,6 +64,23 @@ int launch_sddmm_typed(const SddmmProblem &P, int variant, int vecs, cudaStream_
     }
     const int nvec = P.Kd / EL::V;
     const int max_vpl = 16 / EL::V;
+    // Paired layout (FP32): each lane fetches two adjacent 16-byte vectors with one 32-byte
+    // load, half the lanes per entry of the one-vector layout (so one reduce-scatter round
+    // less and twice the entries per step) and half its load instructions.  Rows of 8 to 64
+    // vectors, 32-byte aligned X and Y rows.  Measured on 65,536^2 at 99%, Kd = 32: 0.299
+    // against 0.347 ms (4.5 against 6.6 warp instructions per entry); at 16,384^2, Kd = 256:
+    // 1% to 9% faster.  BF16 measured slower paired (Kd = 32: 0.262 against 0.235 ms; Kd =
+    // 256: 2-4%), where the mixed-precision dot already left fewer instructions per entry.
+    const bool pairable = EL::dtype == GBSP_F32 && vecs == 0 && nvec >= 8 && nvec <= 64 && (nvec & (nvec - 1)) == 0 &&
+                          aligned32(P.X) && aligned32(P.Y) && P.ldx % (2 * EL::V) == 0 && P.ldy % (2 * EL::V) == 0;
+    if (pairable && variant != GBSP_VARIANT_ENTRY) {
+        switch (nvec / 2) {
+            case 4: return run<EL, 4, 2, true>(P, variant, s);
+            case 8: return run<EL, 8, 2, true>(P, variant, s);
+            case 16: return run<EL, 16, 2, true>(P, variant, s);
+            case 32: return run<EL, 32, 2, true>(P, variant, s);
+        }
+    }
     // one vector per lane up to 8 vectors (8 lanes x 16 B read a 128-byte row in one
     // wavefront; measured 3% faster than 4 x 2 at Kd = 32 FP32), then 2 or 4
     int vpl = vecs > 0 ? vecs : (nvec >= 32 ? 4 : nvec > 8 ? 2 : 1);

@@ -15,10 +15,13 @@ namespace gbsp {
 namespace sddmm_detail {
 
 // Partial dots of one chunk: part[t] is this lane's share of the dot of entry g * LPN + t.
-template <class EL, int LPN, int VPL, bool CHECK_COLS, bool CHECK_NNZ>
+// PAIR (VPL = 2, full rows only): the lane's two vectors are adjacent and arrive by one
+// 32-byte load.
+template <class EL, int LPN, int VPL, bool CHECK_COLS, bool CHECK_NNZ, bool PAIR = false>
 __device__ __forceinline__ void sddmm_chunk(const uint4 *__restrict__ Yv, int64_t ldv, int c, int cnt, int g,
                                             const bool (&colok)[VPL], const uint4 (&xr)[VPL],
                                             const float (&x)[VPL][EL::V], float (&part)[LPN]) {
+    static_assert(!PAIR || (VPL == 2 && !CHECK_COLS), "paired loads cover whole rows of two vectors per lane");
 #pragma unroll
     for (int t = 0; t < LPN; ++t) part[t] = 0.f;
 #pragma unroll
@@ -28,6 +31,14 @@ __device__ __forceinline__ void sddmm_chunk(const uint4 *__restrict__ Yv, int64_
         const int cj = __shfl_sync(FULL, c, idx);
         const uint4 *rp = Yv + (int64_t)cj * ldv;
         uint4 raw[VPL];
+        if constexpr (PAIR) {
+            if (!CHECK_NNZ || idx < cnt) {
+                ld_gather32(rp, raw[0], raw[VPL - 1]);
+            } else {
+                raw[0] = make_uint4(0, 0, 0, 0);
+                raw[VPL - 1] = raw[0];
+            }
+        } else
 #pragma unroll
         for (int v = 0; v < VPL; ++v) {
             if constexpr (CHECK_COLS || CHECK_NNZ) {
@@ -50,12 +61,14 @@ __device__ __forceinline__ void sddmm_chunk(const uint4 *__restrict__ Yv, int64_
 // column indices and values prefetched while the current ones are used.  With POS, entry
 // e's value and output sit at position P.pos[e] of the caller's arrays (a sub-matrix of
 // another CSR, such as the residual of a tensor-core plan).
-template <class EL, int LPN, int VPL, bool CHECK_COLS, bool POS = false>
+template <class EL, int LPN, int VPL, bool CHECK_COLS, bool POS = false, bool PAIR = false>
 __device__ __forceinline__ void sddmm_segment(const SddmmProblem &P, int row, int64_t p0, int64_t p1, int lane) {
     const int sl = lane % LPN, g = lane / LPN;
     using ST = typename EL::stored;
     const ST *X = static_cast<const ST *>(P.X);
-    const uint4 *Yv = static_cast<const uint4 *>(P.Y) + sl;
+    // a lane's vectors: v * LPN + sl (each instruction of a group reads one contiguous span),
+    // or 2 * sl + v when paired (one 32-byte load per lane)
+    const uint4 *Yv = static_cast<const uint4 *>(P.Y) + (PAIR ? 2 * sl : sl);
     const int64_t ldv = P.ldy / EL::V;
 
     bool colok[VPL];
@@ -63,7 +76,7 @@ __device__ __forceinline__ void sddmm_segment(const SddmmProblem &P, int row, in
     float x[VPL][EL::V];
 #pragma unroll
     for (int v = 0; v < VPL; ++v) {
-        const int k0 = (v * LPN + sl) * EL::V;
+        const int k0 = (PAIR ? 2 * sl + v : v * LPN + sl) * EL::V;
         colok[v] = !CHECK_COLS || k0 < P.Kd;
         xr[v] = make_uint4(0, 0, 0, 0);
         if (colok[v]) xr[v] = ld_gather16(X + (int64_t)row * P.ldx + k0);
@@ -91,9 +104,9 @@ __device__ __forceinline__ void sddmm_segment(const SddmmProblem &P, int row, in
         }
         float part[LPN];
         if (nb <= p1)
-            sddmm_chunk<EL, LPN, VPL, CHECK_COLS, false>(Yv, ldv, c, 32, g, colok, xr, x, part);
+            sddmm_chunk<EL, LPN, VPL, CHECK_COLS, false, PAIR>(Yv, ldv, c, 32, g, colok, xr, x, part);
         else
-            sddmm_chunk<EL, LPN, VPL, CHECK_COLS, true>(Yv, ldv, c, (int)(p1 - base), g, colok, xr, x, part);
+            sddmm_chunk<EL, LPN, VPL, CHECK_COLS, true, PAIR>(Yv, ldv, c, (int)(p1 - base), g, colok, xr, x, part);
 #pragma unroll
         for (int h = LPN / 2; h >= 1; h >>= 1) {
             const bool upper = (sl & h) != 0;
@@ -115,23 +128,28 @@ __device__ __forceinline__ void sddmm_segment(const SddmmProblem &P, int row, in
     }
 }
 
-// One warp per row of S.
-template <class EL, int LPN, int VPL, bool POS = false>
+// One warp per row of S.  PAIR requires Kd = LPN * 2 * V with 32-byte aligned rows of X and Y
+// (the launcher checks).
+template <class EL, int LPN, int VPL, bool POS = false, bool PAIR = false>
 __global__ void __launch_bounds__(256) sddmm_rowsplit_kernel(const SddmmProblem P) {
     const int lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= P.M) return;
     const int64_t p0 = __ldg(P.rowptr + row), p1 = __ldg(P.rowptr + row + 1);
-    if (P.Kd == LPN * VPL * EL::V)
-        sddmm_segment<EL, LPN, VPL, false, POS>(P, row, p0, p1, lane);
-    else
-        sddmm_segment<EL, LPN, VPL, true, POS>(P, row, p0, p1, lane);
+    if constexpr (PAIR) {
+        sddmm_segment<EL, LPN, VPL, false, POS, true>(P, row, p0, p1, lane);
+    } else {
+        if (P.Kd == LPN * VPL * EL::V)
+            sddmm_segment<EL, LPN, VPL, false, POS>(P, row, p0, p1, lane);
+        else
+            sddmm_segment<EL, LPN, VPL, true, POS>(P, row, p0, p1, lane);
+    }
 }
 
 // nnz-balanced split: warp w takes the items [w * ipw, (w + 1) * ipw) of the merge path
 // over (row ends, stored entries) and computes every entry in it, row segment by row
 // segment.  Each output belongs to one entry, so no carries are needed.
-template <class EL, int LPN, int VPL>
+template <class EL, int LPN, int VPL, bool PAIR = false>
 __global__ void __launch_bounds__(256) sddmm_merge_kernel(const SddmmProblem P, int nwarps) {
     const int lane = threadIdx.x & 31;
     const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -148,7 +166,9 @@ __global__ void __launch_bounds__(256) sddmm_merge_kernel(const SddmmProblem P, 
     for (int row = x0; row <= x1 && row < P.M; ++row) {
         const int64_t e = row < x1 ? (int64_t)__ldg(P.rowptr + row + 1) : y1;
         if (e > p) {
-            if (full)
+            if constexpr (PAIR)
+                sddmm_segment<EL, LPN, VPL, false, false, true>(P, row, p, e, lane);
+            else if (full)
                 sddmm_segment<EL, LPN, VPL, false>(P, row, p, e, lane);
             else
                 sddmm_segment<EL, LPN, VPL, true>(P, row, p, e, lane);

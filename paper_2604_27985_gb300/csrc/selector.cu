@@ -292,7 +292,9 @@ __global__ void __launch_bounds__(256) mlp_train_kernel(float *w, float *adam, c
 // The 24 SpMM variants the selector chooses among (index -> options):
 //   0..8   row-split, vecs {1,2,4} x unroll {2,4,8}
 //   9..17  merge path, vecs {1,2,4} x unroll {2,4,8}
-//   18..21 merge path with 1 or 2 CTAs per SM, vecs {1,2}, unroll 4
+//   18..20 merge path with 1 CTA per SM, vecs {1,2}, and with 2 CTAs per SM, vecs 1; unroll 4
+//   21     the SELL-C-sigma plan, C = 64, one sort window (gbsp_sell_plan_*; FP32 only),
+//          variant GBSP_VARIANT_SELL_PLAN
 //   22     row groups (several short rows per warp), default layout
 //   23     the hyper-sparse plan (gbsp_hsp_plan_*; FP32 only), variant GBSP_VARIANT_HSP_PLAN
 int variant_opts(int v, gbsp_opts *o) {
@@ -304,11 +306,15 @@ int variant_opts(int v, gbsp_opts *o) {
         o->unroll = unr[v % 3];
         return GBSP_OK;
     }
-    if (v >= 18 && v < 22) {
+    if (v >= 18 && v < 21) {
         o->variant = GBSP_VARIANT_MERGE;
         o->ctas_per_sm = 1 + (v - 18) / 2;
         o->vecs = 1 + (v - 18) % 2;
         o->unroll = 4;
+        return GBSP_OK;
+    }
+    if (v == 21) {
+        o->variant = GBSP_VARIANT_SELL_PLAN;
         return GBSP_OK;
     }
     if (v == 22) {
@@ -439,6 +445,13 @@ GBSP_EXPORT int gbsp_autotune(const gbsp_csr *A, const gbsp_dense *B, gbsp_dense
                 continue;
             ran = time_variant([&] { return gbsp_hsp_plan_execute(plan, B, C, stream); }, reps, s, e0, e1, &ms, &st);
             gbsp_hsp_plan_destroy(plan);
+        } else if (o.variant == GBSP_VARIANT_SELL_PLAN) {
+            gbsp_sell_plan *plan = nullptr;
+            if (A->dtype != GBSP_F32 || B->dtype != GBSP_F32 || A->nnz < 0 ||
+                gbsp_sell_plan_create(A, 64, 0, stream, &plan) != GBSP_OK)
+                continue;
+            ran = time_variant([&] { return gbsp_sell_plan_execute(plan, B, C, stream); }, reps, s, e0, e1, &ms, &st);
+            gbsp_sell_plan_destroy(plan);
         } else {
             ran = time_variant([&] { return spmm_csr_ex(A, B, C, &o, stream); }, reps, s, e0, e1, &ms, &st);
         }

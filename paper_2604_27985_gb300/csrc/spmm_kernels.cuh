@@ -24,15 +24,24 @@ __device__ __forceinline__ float coef(const SpmmProblem &P, int64_t p, int c) {
     return a;
 }
 
+// Where a lane's vectors sit in its group's column tile: vector v * LPN + sl (each load
+// instruction of a group reads one contiguous span), or, paired (VPL = 2), 2 * sl + v, the
+// two adjacent vectors arriving by one 32-byte load.
+template <int LPN, bool PAIR>
+__device__ __forceinline__ int lane_vec(int sl, int v) {
+    return PAIR ? 2 * sl + v : v * LPN + sl;
+}
+
 // One step of a group: U nonzeros per group (G * U per warp), VPL 16-byte vectors per lane
 // each.  CHECK_NNZ guards a partial chunk (entries past cnt are skipped), CHECK_COLS a
 // partial column tile (vectors past N are skipped); the full-chunk, full-tile case issues
-// its loads unpredicated.
-template <class EL, int LPN, int VPL, int U, bool CHECK_COLS, bool CHECK_NNZ>
+// its loads unpredicated.  Bv points at the lane's first vector (lane_vec(sl, 0)).
+template <class EL, int LPN, int VPL, int U, bool CHECK_COLS, bool CHECK_NNZ, bool PAIR = false>
 __device__ __forceinline__ void gather_step(const uint4 *__restrict__ Bv, int64_t ldv, int c, float a, int q,
                                             int cnt, int sub, const bool (&colok)[VPL],
                                             float (&acc)[VPL][EL::V]) {
     constexpr int G = 32 / LPN;
+    static_assert(!PAIR || VPL == 2, "pairs are two vectors");
     uint4 raw[U][VPL];
     float aj[U];
 #pragma unroll
@@ -41,6 +50,21 @@ __device__ __forceinline__ void gather_step(const uint4 *__restrict__ Bv, int64_
         const int cj = __shfl_sync(FULL, c, idx);
         aj[u] = __shfl_sync(FULL, a, idx);
         const uint4 *rp = Bv + (int64_t)cj * ldv;
+        if constexpr (PAIR) {
+            bool ok = true, ok1 = true;
+            if constexpr (CHECK_NNZ) ok = idx < cnt;
+            if constexpr (CHECK_COLS) {
+                ok1 = ok && colok[VPL - 1];
+                ok = ok && colok[0];
+            }
+            if (ok1) {
+                ld_gather32(rp, raw[u][0], raw[u][VPL - 1]);
+            } else {  // the tile's last pair is cut by N (or the entry is past the chunk)
+                raw[u][0] = ok ? ld_gather16(rp) : make_uint4(0, 0, 0, 0);
+                raw[u][VPL - 1] = make_uint4(0, 0, 0, 0);
+            }
+            continue;
+        }
 #pragma unroll
         for (int v = 0; v < VPL; ++v) {
             if constexpr (CHECK_COLS || CHECK_NNZ) {
@@ -62,7 +86,7 @@ __device__ __forceinline__ void gather_step(const uint4 *__restrict__ Bv, int64_
 
 // Accumulates the stored entries [p0, p1) of one row into acc (the lane's VPL vectors of
 // the row's column tile starting at col_base).
-template <class EL, int LPN, int VPL, int U, bool CHECK_COLS>
+template <class EL, int LPN, int VPL, int U, bool CHECK_COLS, bool PAIR = false>
 __device__ __forceinline__ void gather_range(const SpmmProblem &P, int64_t p0, int64_t p1,
                                              float (&acc)[VPL][EL::V], int lane, int col_base) {
     constexpr int G = 32 / LPN;
@@ -73,7 +97,8 @@ __device__ __forceinline__ void gather_range(const SpmmProblem &P, int64_t p0, i
     const int64_t ldv = P.ldb / EL::V;
     bool colok[VPL];
 #pragma unroll
-    for (int v = 0; v < VPL; ++v) colok[v] = col_base + v * LPN * EL::V < P.N;
+    for (int v = 0; v < VPL; ++v)
+        colok[v] = col_base + (lane_vec<LPN, PAIR>(0, v) - lane_vec<LPN, PAIR>(0, 0)) * EL::V < P.N;
 
     int c = 0;
     float a = 0.f;
@@ -93,7 +118,7 @@ __device__ __forceinline__ void gather_range(const SpmmProblem &P, int64_t p0, i
         if (nb <= p1) {
 #pragma unroll
             for (int q = 0; q < 32; q += STEP)
-                gather_step<EL, LPN, VPL, U, CHECK_COLS, false>(Bv, ldv, c, a, q, 32, sub, colok, acc);
+                gather_step<EL, LPN, VPL, U, CHECK_COLS, false, PAIR>(Bv, ldv, c, a, q, 32, sub, colok, acc);
         } else {
             // the row's last, partial chunk: whole steps unchecked, then the rest (fewer than
             // STEP entries) in one predicated step, so its U gathers per lane are in flight
@@ -102,8 +127,9 @@ __device__ __forceinline__ void gather_range(const SpmmProblem &P, int64_t p0, i
             int q = 0;
 #pragma unroll 1
             for (; q + STEP <= cnt; q += STEP)
-                gather_step<EL, LPN, VPL, U, CHECK_COLS, false>(Bv, ldv, c, a, q, cnt, sub, colok, acc);
-            if (q < cnt) gather_step<EL, LPN, VPL, U, CHECK_COLS, true>(Bv, ldv, c, a, q, cnt, sub, colok, acc);
+                gather_step<EL, LPN, VPL, U, CHECK_COLS, false, PAIR>(Bv, ldv, c, a, q, cnt, sub, colok, acc);
+            if (q < cnt)
+                gather_step<EL, LPN, VPL, U, CHECK_COLS, true, PAIR>(Bv, ldv, c, a, q, cnt, sub, colok, acc);
         }
         base = nb;
         c = c2;
@@ -122,13 +148,13 @@ __device__ __forceinline__ void reduce_groups(float (&acc)[VPL][EL::V]) {
             for (int k = 0; k < EL::V; ++k) acc[v][k] += __shfl_xor_sync(FULL, acc[v][k], off);
 }
 
-template <class EL, int LPN, int VPL>
+template <class EL, int LPN, int VPL, bool PAIR = false>
 __device__ __forceinline__ void store_row(float *dst_row, const float (&acc)[VPL][EL::V], int lane,
                                           int col_base, int N, float scale) {
     if (lane >= LPN) return;
 #pragma unroll
     for (int v = 0; v < VPL; ++v) {
-        const int col = col_base + v * LPN * EL::V;
+        const int col = col_base + (lane_vec<LPN, PAIR>(0, v) - lane_vec<LPN, PAIR>(0, 0)) * EL::V;
         if (col < N) {
 #pragma unroll
             for (int k = 0; k < EL::V; k += 4)
@@ -144,13 +170,14 @@ __device__ __forceinline__ float row_scale(const SpmmProblem &P, int row) {
     return EL::dtype == GBSP_E4M3 ? __ldg(P.a_scale + row) : 1.0f;
 }
 
-// One warp per row; blockIdx.y is the column tile.
-template <class EL, int LPN, int VPL, int U>
+// One warp per row; blockIdx.y is the column tile.  PAIR: 32-byte aligned B rows (the
+// launcher checks).
+template <class EL, int LPN, int VPL, int U, bool PAIR = false>
 __global__ void __launch_bounds__(256) spmm_rowsplit_kernel(const SpmmProblem P) {
     const int lane = threadIdx.x & 31;
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (row >= P.M) return;
-    const int col_base = blockIdx.y * (LPN * VPL * EL::V) + (lane % LPN) * EL::V;
+    const int col_base = blockIdx.y * (LPN * VPL * EL::V) + lane_vec<LPN, PAIR>(lane % LPN, 0) * EL::V;
     float acc[VPL][EL::V];
 #pragma unroll
     for (int v = 0; v < VPL; ++v)
@@ -158,11 +185,11 @@ __global__ void __launch_bounds__(256) spmm_rowsplit_kernel(const SpmmProblem P)
         for (int k = 0; k < EL::V; ++k) acc[v][k] = 0.f;
     const int64_t p0 = __ldg(P.rowptr + row), p1 = __ldg(P.rowptr + row + 1);
     if ((blockIdx.y + 1) * (LPN * VPL * EL::V) <= P.N)
-        gather_range<EL, LPN, VPL, U, false>(P, p0, p1, acc, lane, col_base);
+        gather_range<EL, LPN, VPL, U, false, PAIR>(P, p0, p1, acc, lane, col_base);
     else
-        gather_range<EL, LPN, VPL, U, true>(P, p0, p1, acc, lane, col_base);
+        gather_range<EL, LPN, VPL, U, true, PAIR>(P, p0, p1, acc, lane, col_base);
     reduce_groups<EL, LPN, VPL>(acc);
-    store_row<EL, LPN, VPL>(P.C + (int64_t)row * P.ldc, acc, lane, col_base, P.N, row_scale<EL>(P, row));
+    store_row<EL, LPN, VPL, PAIR>(P.C + (int64_t)row * P.ldc, acc, lane, col_base, P.N, row_scale<EL>(P, row));
 }
 
 // nnz-balanced split: warp w takes the items [w * ipw, (w + 1) * ipw) of the merge path
@@ -170,13 +197,13 @@ __global__ void __launch_bounds__(256) spmm_rowsplit_kernel(const SpmmProblem P)
 // partial sum of the row still open at the range end goes to the carry arrays and is
 // added by spmm_merge_fixup_kernel.  The grid is fixed on the host, nnz is read on the
 // device, so the launch needs no host-side knowledge of the matrix.
-template <class EL, int LPN, int VPL, int U>
+template <class EL, int LPN, int VPL, int U, bool PAIR = false>
 __global__ void __launch_bounds__(256) spmm_merge_kernel(const SpmmProblem P, int32_t *carry_row,
                                                          float *carry_val, int nwarps) {
     constexpr int TW = LPN * VPL * EL::V;
     const int lane = threadIdx.x & 31;
     const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int col_base = blockIdx.y * TW + (lane % LPN) * EL::V;
+    const int col_base = blockIdx.y * TW + lane_vec<LPN, PAIR>(lane % LPN, 0) * EL::V;
     const int64_t nnz = __ldg(P.rowptr + P.M);
     const int64_t total = (int64_t)P.M + nnz;
     const int64_t ipw = (total + nwarps - 1) / nwarps;
@@ -195,11 +222,11 @@ __global__ void __launch_bounds__(256) spmm_merge_kernel(const SpmmProblem P, in
     for (int row = x0; row < x1; ++row) {
         const int64_t e = __ldg(P.rowptr + row + 1);
         if (full_tile)
-            gather_range<EL, LPN, VPL, U, false>(P, p, e, acc, lane, col_base);
+            gather_range<EL, LPN, VPL, U, false, PAIR>(P, p, e, acc, lane, col_base);
         else
-            gather_range<EL, LPN, VPL, U, true>(P, p, e, acc, lane, col_base);
+            gather_range<EL, LPN, VPL, U, true, PAIR>(P, p, e, acc, lane, col_base);
         reduce_groups<EL, LPN, VPL>(acc);
-        store_row<EL, LPN, VPL>(P.C + (int64_t)row * P.ldc, acc, lane, col_base, P.N, row_scale<EL>(P, row));
+        store_row<EL, LPN, VPL, PAIR>(P.C + (int64_t)row * P.ldc, acc, lane, col_base, P.N, row_scale<EL>(P, row));
 #pragma unroll
         for (int v = 0; v < VPL; ++v)
 #pragma unroll
@@ -207,9 +234,9 @@ __global__ void __launch_bounds__(256) spmm_merge_kernel(const SpmmProblem P, in
         p = e;
     }
     if (full_tile)
-        gather_range<EL, LPN, VPL, U, false>(P, p, y1, acc, lane, col_base);
+        gather_range<EL, LPN, VPL, U, false, PAIR>(P, p, y1, acc, lane, col_base);
     else
-        gather_range<EL, LPN, VPL, U, true>(P, p, y1, acc, lane, col_base);
+        gather_range<EL, LPN, VPL, U, true, PAIR>(P, p, y1, acc, lane, col_base);
     reduce_groups<EL, LPN, VPL>(acc);
     float *cv = carry_val + ((int64_t)blockIdx.y * nwarps + w) * TW;
     if (lane < LPN) {
@@ -217,7 +244,7 @@ __global__ void __launch_bounds__(256) spmm_merge_kernel(const SpmmProblem P, in
         for (int v = 0; v < VPL; ++v)
 #pragma unroll
             for (int k = 0; k < EL::V; k += 4)
-                *reinterpret_cast<float4 *>(cv + (lane + v * LPN) * EL::V + k) =
+                *reinterpret_cast<float4 *>(cv + lane_vec<LPN, PAIR>(lane, v) * EL::V + k) =
                     make_float4(acc[v][k], acc[v][k + 1], acc[v][k + 2], acc[v][k + 3]);
     }
     if (lane == 0 && blockIdx.y == 0) carry_row[w] = (d0 < d1 && x1 < P.M) ? x1 : -1;

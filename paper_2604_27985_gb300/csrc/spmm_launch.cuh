@@ -7,15 +7,15 @@
 namespace gbsp {
 namespace spmm_detail {
 
-template <class EL, int LPN, int VPL, int U, int ALGO>
+template <class EL, int LPN, int VPL, int U, int ALGO, bool PAIR = false>
 int run(const SpmmProblem &P, int ctas_per_sm, cudaStream_t s) {
     constexpr int TW = LPN * VPL * EL::V;
     const int ntiles = (P.N + TW - 1) / TW;
     if constexpr (ALGO == GBSP_VARIANT_MERGE) {
         int per_sm = ctas_per_sm;
         if (per_sm <= 0) {
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spmm_merge_kernel<EL, LPN, VPL, U>, 256, 0) !=
-                cudaSuccess)
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spmm_merge_kernel<EL, LPN, VPL, U, PAIR>, 256,
+                                                              0) != cudaSuccess)
                 return check_launch("occupancy query");
             per_sm = per_sm < 1 ? 1 : per_sm;
         }
@@ -29,7 +29,7 @@ int run(const SpmmProblem &P, int ctas_per_sm, cudaStream_t s) {
             scratch_free(cr, s);
             return st;
         }
-        spmm_merge_kernel<EL, LPN, VPL, U><<<dim3(nblocks, ntiles), 256, 0, s>>>(
+        spmm_merge_kernel<EL, LPN, VPL, U, PAIR><<<dim3(nblocks, ntiles), 256, 0, s>>>(
             P, static_cast<int32_t *>(cr), static_cast<float *>(cv), nwarps);
         spmm_merge_fixup_kernel<EL><<<dim3((nwarps + 7) / 8, ntiles), 256, 0, s>>>(
             P, static_cast<const int32_t *>(cr), static_cast<const float *>(cv), nwarps, TW);
@@ -45,7 +45,7 @@ int run(const SpmmProblem &P, int ctas_per_sm, cudaStream_t s) {
         count_launches(1);
         return check_launch("spmm rowgroup");
     } else {
-        spmm_rowsplit_kernel<EL, LPN, VPL, U><<<dim3((P.M + 7) / 8, ntiles), 256, 0, s>>>(P);
+        spmm_rowsplit_kernel<EL, LPN, VPL, U, PAIR><<<dim3((P.M + 7) / 8, ntiles), 256, 0, s>>>(P);
         count_launches(1);
         return check_launch("spmm rowsplit");
     }
@@ -53,33 +53,33 @@ int run(const SpmmProblem &P, int ctas_per_sm, cudaStream_t s) {
 
 // Gathers in flight per lane: U <= LPN keeps a step inside one chunk of 32 nonzeros,
 // VPL * U <= 16 bounds the registers holding loads in flight.
-template <class EL, int LPN, int VPL, int ALGO>
+template <class EL, int LPN, int VPL, int ALGO, bool PAIR = false>
 int by_unroll(const SpmmProblem &P, int u, int cps, cudaStream_t s) {
     constexpr int UMAX = LPN < 16 / VPL ? LPN : 16 / VPL;
     if constexpr (UMAX >= 8) {
-        if (u >= 8) return run<EL, LPN, VPL, 8, ALGO>(P, cps, s);
+        if (u >= 8) return run<EL, LPN, VPL, 8, ALGO, PAIR>(P, cps, s);
     }
     if constexpr (UMAX >= 4) {
-        if (u >= 4) return run<EL, LPN, VPL, 4, ALGO>(P, cps, s);
+        if (u >= 4) return run<EL, LPN, VPL, 4, ALGO, PAIR>(P, cps, s);
     }
     if constexpr (UMAX >= 2) {
-        return run<EL, LPN, VPL, 2, ALGO>(P, cps, s);
+        return run<EL, LPN, VPL, 2, ALGO, PAIR>(P, cps, s);
     } else {
-        return run<EL, LPN, VPL, 1, ALGO>(P, cps, s);
+        return run<EL, LPN, VPL, 1, ALGO, PAIR>(P, cps, s);
     }
 }
 
-template <class EL, int VPL, int ALGO>
+template <class EL, int VPL, int ALGO, bool PAIR = false>
 int by_lanes(const SpmmProblem &P, int lpn, int u, int cps, cudaStream_t s) {
     if constexpr (VPL * EL::V > 16) {  // at most 16 accumulators per lane
         return fail(GBSP_ERR_UNSUPPORTED, "spmm: %d vectors per lane exceed 16 elements", VPL);
     } else switch (lpn) {
         case 1: if constexpr (VPL == 1) return by_unroll<EL, 1, 1, ALGO>(P, u, cps, s); break;
         case 2: if constexpr (VPL == 1) return by_unroll<EL, 2, 1, ALGO>(P, u, cps, s); break;
-        case 4: if constexpr (VPL <= 2) return by_unroll<EL, 4, VPL, ALGO>(P, u, cps, s); break;
-        case 8: return by_unroll<EL, 8, VPL, ALGO>(P, u, cps, s);
-        case 16: return by_unroll<EL, 16, VPL, ALGO>(P, u, cps, s);
-        case 32: return by_unroll<EL, 32, VPL, ALGO>(P, u, cps, s);
+        case 4: if constexpr (VPL <= 2) return by_unroll<EL, 4, VPL, ALGO, PAIR>(P, u, cps, s); break;
+        case 8: return by_unroll<EL, 8, VPL, ALGO, PAIR>(P, u, cps, s);
+        case 16: return by_unroll<EL, 16, VPL, ALGO, PAIR>(P, u, cps, s);
+        case 32: return by_unroll<EL, 32, VPL, ALGO, PAIR>(P, u, cps, s);
     }
     return fail(GBSP_ERR_UNSUPPORTED, "spmm: no kernel for %d lanes x %d vectors", lpn, VPL);
 }
@@ -108,6 +108,23 @@ int launch_spmm_algo(const SpmmProblem &P, int vecs, int unroll, int ctas_per_sm
     using namespace spmm_detail;
     int lpn, vpl;
     spmm_layout(P.N / EL::V, vecs, 16 / EL::V, lpn, vpl);  // N % V == 0 is checked by the caller
+    // Default layout with 32-byte aligned B rows (row split and merge path): each lane's two
+    // vectors are adjacent and arrive by one 32-byte load, half the load instructions; a
+    // 128-byte row then takes 4 lanes (8 entries per step) instead of 8.  Explicit vecs keep
+    // the strided layout.
+    if constexpr (ALGO != GBSP_VARIANT_ROWGROUP && 2 * EL::V <= 16) {
+        if (vecs == 0 && aligned32(P.B) && P.ldb % (2 * EL::V) == 0) {
+            const int nvec = P.N / EL::V;
+            if (nvec == 8) {
+                lpn = 4;
+                vpl = 2;
+            }
+            if (vpl == 2) {
+                const int u = unroll > 0 ? unroll : 4;
+                return by_lanes<EL, 2, ALGO, true>(P, lpn, u, ctas_per_sm, s);
+            }
+        }
+    }
     const int u = unroll > 0 ? unroll : (vpl == 1 ? 8 : 4);
     switch (vpl) {
         case 1: return by_lanes<EL, 1, ALGO>(P, lpn, u, ctas_per_sm, s);

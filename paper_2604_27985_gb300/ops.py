@@ -413,16 +413,20 @@ N_PARAMS = 16 * 64 + 64 + 64 * 64 + 64 + 24 * 64 + 24
 
 N_SDDMM_VARIANTS = 9
 HSP_PLAN = "hsp_plan"
+SELL_PLAN = "sell_plan"
 
 
 def variant_options(v: int) -> dict:
     """spmm keyword arguments of selector variant v (gbsp_variant_opts); variant 23, the
-    hyper-sparse plan, comes back as {"variant": "hsp_plan"} (build an HspPlan and execute
-    it instead of calling spmm)."""
+    hyper-sparse plan, comes back as {"variant": "hsp_plan"} and variant 21, the SELL-C-sigma
+    plan, as {"variant": "sell_plan"} (build the plan and execute it instead of calling
+    spmm)."""
     o = Opts()
     check(lib.gbsp_variant_opts(int(v), ctypes.byref(o)))
     if o.variant == 6:
         return {"variant": HSP_PLAN}
+    if o.variant == 7:
+        return {"variant": SELL_PLAN}
     name = {1: "rowsplit", 2: "merge", 3: "scalar", 5: "rowgroup"}[o.variant]
     return {"variant": name, "vecs": o.vecs, "unroll": o.unroll, "ctas_per_sm": o.ctas_per_sm}
 

@@ -69,11 +69,11 @@ def label(rowptr, colidx, vals, ncols, N, dtype, reps=3, stream=None, op="spmm")
 
 
 def applicable(op, dtype):
-    """Variant indices the model may choose for this op and dtype: SDDMM has 9; the
-    hyper-sparse plan (SpMM variant 23) takes FP32 only."""
+    """Variant indices the model may choose for this op and dtype: SDDMM has 9; the SELL-C-
+    sigma and hyper-sparse plans (SpMM variants 21 and 23) take FP32 only."""
     if op == "sddmm":
         return np.arange(ops.N_SDDMM_VARIANTS)
-    return np.arange(ops.N_VARIANTS) if dtype == F32 else np.arange(ops.N_VARIANTS - 1)
+    return np.arange(ops.N_VARIANTS) if dtype == F32 else np.setdiff1d(np.arange(ops.N_VARIANTS), [21, 23])
 
 
 class Selector:
@@ -196,12 +196,15 @@ class Selector:
         return self.run_spmm(v, rowptr, colidx, vals, B, out, **kw)
 
     def run_spmm(self, v, rowptr, colidx, vals, B, out, stream=None):
-        """Runs SpMM variant v (23: the hyper-sparse plan, built once per pattern)."""
+        """Runs SpMM variant v (21 / 23: the SELL-C-sigma / hyper-sparse plan, built once per
+        pattern; a SELL plan copies the values, so it is rebuilt if they are to change)."""
         opts = ops.variant_options(v)
-        if opts["variant"] == ops.HSP_PLAN:
-            key = (rowptr.data_ptr(), colidx.data_ptr(), vals.data_ptr(), rowptr.numel(), colidx.numel())
+        if opts["variant"] in (ops.HSP_PLAN, ops.SELL_PLAN):
+            key = (opts["variant"], rowptr.data_ptr(), colidx.data_ptr(), vals.data_ptr(), rowptr.numel(),
+                   colidx.numel())
             if key not in self._plans:
-                self._plans[key] = ops.HspPlan(rowptr, colidx, vals, B.shape[0], stream=stream)
+                make = ops.HspPlan if opts["variant"] == ops.HSP_PLAN else ops.SellPlan
+                self._plans[key] = make(rowptr, colidx, vals, B.shape[0], stream=stream)
             return self._plans[key].execute(B, out=out, stream=stream)
         return ops.spmm(rowptr, colidx, vals, B, out=out, stream=stream, **opts)
 

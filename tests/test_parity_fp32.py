@@ -63,7 +63,7 @@ def run_spmm(gb, A, B, **kw):
 
 
 @pytest.mark.parametrize("name", list(MATS))
-@pytest.mark.parametrize("N", [4, 16, 32, 64, 96, 128, 256, 264])
+@pytest.mark.parametrize("N", [4, 16, 32, 64, 68, 96, 128, 132, 256, 264])
 @pytest.mark.parametrize("variant", ["rowsplit", "merge"])
 def test_spmm_fp32(gb, name, N, variant):
     A = mat(name)
@@ -348,3 +348,19 @@ def test_sddmm_full_size_sampled_rows(gb, big):
     rp, ci, v, idx = sub_csr(S.rowptr, S.colidx, S.vals, rows)
     ref, scale = oracle.sddmm(rp, ci, v, X[rows], Y)
     assert_within(out[idx], ref, scale, TOL, "full-size sddmm")
+
+
+@pytest.mark.parametrize("N", [64, 128, 256])
+def test_paired_default_layout_matches_strided_bitwise(gb, N):
+    """With 32-byte aligned B the default layout fetches each lane's two vectors with one
+    32-byte load; from 16 vectors per row on it keeps the strided layout's lane groups and
+    per-column order, so the two give the same bits (the merge path with the same grid:
+    its default grid follows each kernel's occupancy, and the split of the merge path sets
+    where carries are added)."""
+    A = gen.csr_powerlaw(3000, 2500, 0.99, seed=781)
+    B = gen.dense_normal(A.K, N, 782)
+    rp, ci, v, Bd = dev(A.rowptr), dev(A.colidx), dev(A.vals), dev(B)
+    for variant, cps in (("rowsplit", 0), ("merge", 2)):
+        paired = gb.spmm(rp, ci, v, Bd, variant=variant, ctas_per_sm=cps).cpu().numpy()
+        strided = gb.spmm(rp, ci, v, Bd, variant=variant, ctas_per_sm=cps, vecs=2).cpu().numpy()
+        assert np.array_equal(paired, strided)

@@ -117,10 +117,12 @@ def test_autotune_bookkeeping(gb):
         out = gb.spmm(dev(A.rowptr), dev(A.colidx), dev(A.vals), dev(B), **kw).cpu().numpy()
         assert_within(out, ref, sc, 1e-5, f"variant {v}")
     assert gb.variant_options(22)["variant"] == "rowgroup" and gb.variant_options(23) == {"variant": "hsp_plan"}
-    # BF16: the hyper-sparse plan (FP32 only) does not apply
+    assert gb.variant_options(21) == {"variant": "sell_plan"}
+    # BF16: the SELL-C-sigma and hyper-sparse plans (FP32 only) do not apply
     times16, best16 = gb.autotune(dev(A.rowptr), dev(A.colidx), gb.quantize_bf16(dev(A.vals)),
                                   gb.quantize_bf16(dev(B)), C, reps=1)
-    assert np.isinf(times16[23]) and all(np.isfinite(times16[:23])) and best16 == int(np.argmin(times16))
+    assert np.isinf(times16[21]) and np.isinf(times16[23]) and best16 == int(np.argmin(times16))
+    assert all(np.isfinite(np.delete(times16, [21, 23])))
 
 
 def test_autotune_sddmm_bookkeeping(gb):
@@ -194,7 +196,7 @@ def test_selector_fallback_when_top_two_are_close(gb):
     assert s2.counts["autotuned"] == 0
 
 
-def test_selector_runs_the_hyper_sparse_plan_variant(gb):
+def test_selector_runs_the_plan_variants(gb):
     from _util import assert_within
 
     s = _untrained("spmm")
@@ -202,10 +204,11 @@ def test_selector_runs_the_hyper_sparse_plan_variant(gb):
     B = gen.dense_normal(A.K, 64, 621)
     rp, ci, v, Bd = dev(A.rowptr), dev(A.colidx), dev(A.vals), dev(B)
     ref, sc = oracle.spmm(A.rowptr, A.colidx, A.vals, B)
-    for _ in range(2):  # built once, then reused
-        C = s.run_spmm(23, rp, ci, v, Bd, gb.spmm(rp, ci, v, Bd)).cpu().numpy()
-        assert_within(C, ref, sc, 1e-5, "hyper-sparse plan through the selector")
-    assert len(s._plans) == 1
+    for variant in (23, 21):
+        for _ in range(2):  # built once, then reused
+            C = s.run_spmm(variant, rp, ci, v, Bd, gb.spmm(rp, ci, v, Bd)).cpu().numpy()
+            assert_within(C, ref, sc, 1e-5, f"plan variant {variant} through the selector")
+    assert len(s._plans) == 2
 
 
 def test_sddmm_selector_with_fallback(gb):

@@ -87,7 +87,7 @@ def test_sell_unsorted_repeated_padded_ld_and_errors(gb):
     ci = np.array([5, 1, 5, 0, 0, 7, 2, 3], np.int32)  # unsorted, a repeated column
     vals = gen.vals_int(8, 707)
     B = gen.dense_int(8, 16, 708)
-    plan = gb.SellPlan(dev(rp), dev(ci), dev(vals), 8, C=32)
+    plan = gb.SellPlan(dev(rp), dev(ci), dev(vals), 8, C=64)
     Bp = torch.zeros((8, 24), device="cuda")
     Bp[:, :16] = dev(B)
     Cp = torch.full((4, 20), 3.0, device="cuda")
