@@ -36,7 +36,6 @@ constexpr int kATile = 2048;   // bytes of one stage of window values: 16 rows x
 template <bool FP8>
 constexpr int blocks_per_stage() { return FP8 ? 16 : 8; }
 constexpr uint64_t kWaitNs = 1000000000ull;  // a bounded wait gives up after one second
-constexpr int kStagedCols = 1024;  // block columns of a window staged in shared memory
 
 // ---- PTX wrappers ---------------------------------------------------------------------------
 
@@ -210,15 +209,11 @@ __global__ void __launch_bounds__(kTcThreads) tc_window_kernel(const __grid_cons
     uint64_t *done = empty + SH::S;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
 
-    __shared__ int32_t s_cols[kStagedCols];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int w = blockIdx.x;
     const int b0 = a.win_blk[w], b1 = a.win_blk[w + 1];
     const int nch = (b1 - b0) / SH::BPS;
     const int row0 = a.win_row0[w];
-    // the producer reads each block's column from shared memory, not from a dependent
-    // global load per TMA
-    for (int i = tid; i < b1 - b0 && i < kStagedCols; i += blockDim.x) s_cols[i] = a.blk_col[b0 + i];
 
     if (tid == 0) {
         for (int s = 0; s < SH::S; ++s) {
@@ -241,9 +236,13 @@ __global__ void __launch_bounds__(kTcThreads) tc_window_kernel(const __grid_cons
     // together so the four stay in step.  (Gathering the rows with 16-byte copies from four
     // producer warps instead measured 1.9x slower than one TMA copy per block.)
     if (warp == 0 && lane < kIssuers) {
+        static_assert(SH::BPS <= kIssuers, "one block per issuing lane and stage");
         constexpr unsigned kMask = (1u << kIssuers) - 1u;
         bool ok = true;
         int issued = 0;
+        // lane kb copies block kb of every stage: its column for the first stage now, each
+        // next one loaded while the current stage is in flight (no dependent load before a copy)
+        int col = lane < SH::BPS && lane < b1 - b0 ? a.blk_col[b0 + lane] : -1;
         for (int ch = 0; ch < nch; ++ch) {
             const int s = ch % SH::S;
             if (ch >= SH::S) {  // stage's MMAs done
@@ -254,16 +253,19 @@ __global__ void __launch_bounds__(kTcThreads) tc_window_kernel(const __grid_cons
                 }
             }
             uint8_t *bt = smem + s * SH::STAGE;
-            if (ch == a.withhold && blockIdx.x == 0) continue;  // nothing will complete full[s]
+            const int qn = (ch + 1) * SH::BPS + lane;
+            const int col_next = lane < SH::BPS && qn < b1 - b0 ? a.blk_col[b0 + qn] : -1;
+            if (ch == a.withhold && blockIdx.x == 0) {  // nothing will complete full[s]
+                col = col_next;
+                continue;
+            }
             if (lane == 0) {
                 mbar_expect_tx(&full[s], SH::STAGE);
                 bulk_load(bt + SH::BT, a.atiles + (size_t)(b0 / SH::BPS + ch) * kATile, kATile, &full[s]);
             }
             __syncwarp(kMask);
-#pragma unroll 1
-            for (int kb = lane; kb < SH::BPS; kb += kIssuers) {
-                const int q = ch * SH::BPS + kb;
-                const int col = q < kStagedCols ? s_cols[q] : a.blk_col[b0 + q];
+            if (lane < SH::BPS) {
+                const int kb = lane;
                 const int y = col >= 0 ? col * kBC : a.K;  // padding block: rows past K read as zeros
                 if (a.block_box) {
                     tma_load_3d(bt + kb * SH::NFA * 1024, &tmB, &full[s], 0, y, (int)blockIdx.y * SH::NFA);
@@ -274,6 +276,7 @@ __global__ void __launch_bounds__(kTcThreads) tc_window_kernel(const __grid_cons
                                     (FP8 ? 128 : 64) * ((int)blockIdx.y * SH::NFA + fa), y);
                 }
             }
+            col = col_next;
             issued = ch + 1;
         }
         if (!ok && lane == 0) atomicExch(a.err, 1);

@@ -350,16 +350,19 @@ def test_sddmm_full_size_sampled_rows(gb, big):
     assert_within(out[idx], ref, scale, TOL, "full-size sddmm")
 
 
-@pytest.mark.parametrize("N", [64, 128, 256])
-def test_paired_default_layout_matches_strided_bitwise(gb, N):
-    """With 32-byte aligned B the default layout fetches each lane's two vectors with one
-    32-byte load; from 16 vectors per row on it keeps the strided layout's lane groups and
-    per-column order, so the two give the same bits (the merge path with the same grid:
-    its default grid follows each kernel's occupancy, and the split of the merge path sets
-    where carries are added)."""
+@pytest.mark.parametrize("dt", ["f32", "bf16"])
+def test_paired_default_layout_matches_strided_bitwise(gb, dt):
+    """For 128-byte rows with 32-byte aligned B the default layout fetches each lane's two
+    vectors with one 32-byte load; the strided layout with two vectors per lane has the same
+    lane groups and per-column order, so the two give the same bits (the merge path with the
+    same grid: its default grid follows each kernel's occupancy, and the split of the merge
+    path sets where carries are added)."""
     A = gen.csr_powerlaw(3000, 2500, 0.99, seed=781)
+    N = 32 if dt == "f32" else 64
     B = gen.dense_normal(A.K, N, 782)
     rp, ci, v, Bd = dev(A.rowptr), dev(A.colidx), dev(A.vals), dev(B)
+    if dt == "bf16":
+        v, Bd = gb.quantize_bf16(v), gb.quantize_bf16(Bd)
     for variant, cps in (("rowsplit", 0), ("merge", 2)):
         paired = gb.spmm(rp, ci, v, Bd, variant=variant, ctas_per_sm=cps).cpu().numpy()
         strided = gb.spmm(rp, ci, v, Bd, variant=variant, ctas_per_sm=cps, vecs=2).cpu().numpy()
