@@ -594,7 +594,7 @@ def run_gnn(args):
                      torch.empty(A.nnz, dtype=torch.float32, device=dev)))
         flop += 4.0 * A.nnz * N
         gbytes += (A.nnz * (4 + 4 + 4 + 2 * N) + A.M * (4 + 2 * N + 2 * N)) / 1e9
-    plan = gb.GnnPlan(devs, softmax=args.gat)
+    plan = gb.GnnPlan(devs, softmax=args.gat, edges_per_tile=args.gnn_edges_per_tile)
     stream = torch.cuda.current_stream()
     launches0 = gb.launch_count()
     ms = _event_ms(plan.execute, args.steps, args.warmup, stream)
@@ -1132,6 +1132,7 @@ def main():
     ap.add_argument("--precision-layouts", default="uniform,clustered")
     ap.add_argument("--gnn-graphs", type=int, default=512)
     ap.add_argument("--gat", action="store_true", help="gnn workload with the row softmax (GAT-style chain)")
+    ap.add_argument("--gnn-edges-per-tile", type=int, default=0, help="gnn workload: edges per work tile (0: 512)")
     ap.add_argument("--sweep-dense", action="store_true", help="sweep workload: add 65536^2 at 90%%")
     ap.add_argument("--selector-train", type=int, default=2000)
     ap.add_argument("--selector-test", type=int, default=200)

@@ -144,8 +144,7 @@ int spmm_csr_ex(const gbsp_csr *A, const gbsp_dense *B, gbsp_dense *C, const gbs
  * out is float[S->nnz] in CSR order.  X->rows = S->rows, Y->rows = S->cols,
  * X->cols = Y->cols = Kd.  GBSP_VARIANT_AUTO takes the entry split when rows average under 32
  * stored entries, the merge path on skewed rows (coefficient of variation above 1, or a
- * longest row past 16 times the mean and past 256) and on even rows gathered from a Y of more
- * than 192 MB in rows of at least 256 bytes, and the row split otherwise, from the
+ * longest row past 16 times the mean and past 256) and the row split otherwise, from the
  * same kept row statistics as spmm_csr_ex's AUTO (measured, kept and re-measured as
  * described there); unvectorisable operands take the scalar kernel. */
 int sddmm_csr_ex(const gbsp_csr *S, const gbsp_dense *X, const gbsp_dense *Y, float *out,

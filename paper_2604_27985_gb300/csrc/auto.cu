@@ -148,19 +148,17 @@ int auto_spmm_rule(int64_t M, int64_t nnz, int64_t sumsq, int64_t maxlen, int64_
 }
 
 // The SDDMM split: rows averaging under 32 stored entries take the entry split (a row split
-// would leave lanes idle); skewed rows (as for SpMM) the merge path; even rows gathered from
-// a Y of more than 192 MB in rows of at least 256 bytes also the merge path, whose
-// occupancy-sized grid keeps more gathers in flight while they wait on HBM (measured on
-// 1,048,576^2 at 99.99%, Kd = 128: 8.14 ms against 9.04 ms for the row split, which stays
-// ahead at Kd = 32); the rest the row split.
-int auto_sddmm_rule(int64_t M, int64_t nnz, int64_t sumsq, int64_t maxlen, int64_t y_bytes, int64_t row_bytes) {
+// would leave lanes idle); skewed rows (as for SpMM) the merge path; the rest the row split
+// (with the paired FP32 layout it also leads on even rows whose Y overflows L2: 7.69 against
+// 8.02 ms for the merge path on 1,048,576^2 at 99.99%, Kd = 128).  The operand size is
+// accepted for the same signature as the SpMM rule.
+int auto_sddmm_rule(int64_t M, int64_t nnz, int64_t sumsq, int64_t maxlen, int64_t, int64_t) {
     if (M <= 0 || nnz <= 0) return GBSP_VARIANT_ROWSPLIT;
     const double mean = (double)nnz / (double)M;
     const double var = (double)sumsq / (double)M - mean * mean;
     const double cv = var > 0 ? sqrt(var) / mean : 0.0;
     if (mean < 32.0) return GBSP_VARIANT_ENTRY;
     if (cv > 1.0 || (maxlen > 16.0 * mean && maxlen > 256)) return GBSP_VARIANT_MERGE;
-    if (y_bytes > (192LL << 20) && row_bytes >= 256 && maxlen <= 4 * mean + 64) return GBSP_VARIANT_MERGE;
     return GBSP_VARIANT_ROWSPLIT;
 }
 

@@ -39,14 +39,13 @@ __device__ __forceinline__ int lane_vec(int sl, int v) {
 template <class EL, int LPN, int VPL, int U, bool CHECK_COLS, bool CHECK_NNZ, bool PAIR = false>
 __device__ __forceinline__ void gather_step(const uint4 *__restrict__ Bv, int64_t ldv, int c, float a, int q,
                                             int cnt, int sub, const bool (&colok)[VPL],
-                                            float (&acc)[VPL][EL::V], int ucnt = U) {
+                                            float (&acc)[VPL][EL::V]) {
     constexpr int G = 32 / LPN;
     static_assert(!PAIR || VPL == 2, "pairs are two vectors");
     uint4 raw[U][VPL];
     float aj[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        if (CHECK_NNZ && u >= ucnt) break;  // warp-uniform: slots past the chunk's last entry
         const int idx = q + u * G + sub;
         const int cj = __shfl_sync(FULL, c, idx);
         aj[u] = __shfl_sync(FULL, a, idx);
@@ -80,7 +79,6 @@ __device__ __forceinline__ void gather_step(const uint4 *__restrict__ Bv, int64_
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        if (CHECK_NNZ && u >= ucnt) break;
 #pragma unroll
         for (int v = 0; v < VPL; ++v) EL::axpy(aj[u], raw[u][v], acc[v]);
     }
@@ -123,16 +121,18 @@ __device__ __forceinline__ void gather_range(const SpmmProblem &P, int64_t p0, i
                 gather_step<EL, LPN, VPL, U, CHECK_COLS, false, PAIR>(Bv, ldv, c, a, q, 32, sub, colok, acc);
         } else {
             // the row's last, partial chunk: whole steps unchecked, then the rest (fewer than
-            // STEP entries) in one step of ceil(rest / G) slots per lane, whose gathers are
-            // in flight together rather than one round trip each
+            // STEP entries) in predicated steps of UT = U / 2 slots per lane, whose gathers
+            // are in flight together (one round trip per step rather than per entry) while a
+            // short tail wastes at most half of a step's slots
+            constexpr int UT = U > 1 ? U / 2 : 1;
             const int cnt = (int)(p1 - base);
             int q = 0;
 #pragma unroll 1
             for (; q + STEP <= cnt; q += STEP)
                 gather_step<EL, LPN, VPL, U, CHECK_COLS, false, PAIR>(Bv, ldv, c, a, q, cnt, sub, colok, acc);
-            if (q < cnt)
-                gather_step<EL, LPN, VPL, U, CHECK_COLS, true, PAIR>(Bv, ldv, c, a, q, cnt, sub, colok, acc,
-                                                                     (cnt - q + G - 1) / G);
+#pragma unroll 1
+            for (; q < cnt; q += G * UT)
+                gather_step<EL, LPN, VPL, UT, CHECK_COLS, true, PAIR>(Bv, ldv, c, a, q, cnt, sub, colok, acc);
         }
         base = nb;
         c = c2;

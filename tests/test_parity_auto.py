@@ -243,10 +243,9 @@ def test_auto_rule_for_a_b_past_l2(gb):
     assert gb.auto_choice(dev(P.rowptr), P.K, dev(P.colidx), b_bytes=512 << 20, row_bytes=512)[0] == "merge"
 
 
-def test_auto_sddmm_rule_for_a_y_past_l2(gb):
+def test_auto_sddmm_keeps_the_row_split_for_a_y_past_l2(gb):
     A = gen.csr_uniform(4096, 4096, 0.99, seed=663)
     rp, ci = dev(A.rowptr), dev(A.colidx)
     gb.auto_forget()
-    assert gb.auto_choice(rp, A.K, ci, op="sddmm", b_bytes=512 << 20, row_bytes=512)[0] == "merge"
-    assert gb.auto_choice(rp, A.K, ci, op="sddmm", b_bytes=512 << 20, row_bytes=128)[0] == "rowsplit"
-    assert gb.auto_choice(rp, A.K, ci, op="sddmm", b_bytes=64 << 20, row_bytes=512)[0] == "rowsplit"
+    for yb, rb in ((512 << 20, 512), (512 << 20, 128), (64 << 20, 512)):
+        assert gb.auto_choice(rp, A.K, ci, op="sddmm", b_bytes=yb, row_bytes=rb)[0] == "rowsplit"
