@@ -125,8 +125,9 @@ int sddmm_csr(const int32_t *rowptr, const int32_t *colidx, const float *svals, 
  * uneven rows, Section II-D): rows averaging under 12 entries with none past 128 take the
  * row groups, skewed rows (coefficient of variation above 1, or a longest row past 16
  * times the mean and past 256) the merge path, even rows gathered from a B of more than
- * 192 MB (past L2) in rows of at least 256 bytes the row groups, the rest the row split;
- * unvectorisable operands take the scalar kernel.  The row statistics come from one integer pass over
+ * 192 MB (past L2) in rows of at least 256 bytes the row groups, even 128-byte rows from a B
+ * of more than 96 MB the merge path, the rest the row split; unvectorisable operands take
+ * the scalar kernel.  The row statistics come from one integer pass over
  * rowptr.  The first AUTO call on a pattern measures it and waits for the result (a
  * synchronisation); the choice is kept per (device, rowptr, colidx, rows, cols) for the
  * process (64 patterns, oldest dropped first).  Each later call uses the kept choice and

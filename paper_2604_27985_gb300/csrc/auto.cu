@@ -133,9 +133,10 @@ int rule(int op, const int64_t *st, int64_t b_bytes, int64_t row_bytes) {
 // mean and past 256) take the merge path; even rows gathered from a B that overflows L2
 // (more than 192 MB) in rows of at least 256 bytes also take the row groups, whose smaller
 // register footprint keeps more CTAs, and so more gathers, in flight per SM while they wait
-// on HBM (measured on 1,048,576^2 at 99.99%: 2.99 / 6.08 ms against 3.21 / 7.27 ms for the
-// row split at N = 64 / 128, while at N = 32 the row split stays ahead); the rest the row
-// split.
+// on HBM (measured on 1,048,576^2 at 99.99%: 3.02 / 6.17 ms against 3.33 / 7.40 ms for the
+// row split at N = 64 / 128); even rows of 128 bytes from a B past 96 MB take the merge path
+// (same matrix, N = 32: 1.41 against 1.54 ms; on 65,536^2, where B sits in L2, the two are
+// level); the rest the row split.
 int auto_spmm_rule(int64_t M, int64_t nnz, int64_t sumsq, int64_t maxlen, int64_t b_bytes, int64_t row_bytes) {
     if (M <= 0 || nnz <= 0) return GBSP_VARIANT_ROWSPLIT;
     const double mean = (double)nnz / (double)M;
@@ -144,6 +145,7 @@ int auto_spmm_rule(int64_t M, int64_t nnz, int64_t sumsq, int64_t maxlen, int64_
     if (mean < 12.0 && maxlen <= 128) return GBSP_VARIANT_ROWGROUP;
     if (cv > 1.0 || (maxlen > 16.0 * mean && maxlen > 256)) return GBSP_VARIANT_MERGE;
     if (b_bytes > (192LL << 20) && row_bytes >= 256 && maxlen <= 4 * mean + 64) return GBSP_VARIANT_ROWGROUP;
+    if (b_bytes > (96LL << 20) && row_bytes == 128 && maxlen <= 4 * mean + 64) return GBSP_VARIANT_MERGE;
     return GBSP_VARIANT_ROWSPLIT;
 }
 

@@ -232,12 +232,14 @@ def test_auto_follows_a_new_pattern_at_the_same_addresses(gb):
 
 def test_auto_rule_for_a_b_past_l2(gb):
     """Even rows gathered from a B of more than 192 MB in rows of 256 bytes or more take the
-    row groups; 128-byte rows, or a B that fits L2, keep the row split."""
+    row groups, 128-byte rows from a B past 96 MB the merge path; a B that fits L2 keeps the
+    row split."""
     A = gen.csr_uniform(4096, 4096, 0.99, seed=661)
     rp, ci = dev(A.rowptr), dev(A.colidx)
     gb.auto_forget()
     assert gb.auto_choice(rp, A.K, ci, b_bytes=512 << 20, row_bytes=512)[0] == "rowgroup"
-    assert gb.auto_choice(rp, A.K, ci, b_bytes=512 << 20, row_bytes=128)[0] == "rowsplit"
+    assert gb.auto_choice(rp, A.K, ci, b_bytes=512 << 20, row_bytes=128)[0] == "merge"
+    assert gb.auto_choice(rp, A.K, ci, b_bytes=64 << 20, row_bytes=128)[0] == "rowsplit"
     assert gb.auto_choice(rp, A.K, ci, b_bytes=64 << 20, row_bytes=512)[0] == "rowsplit"
     P = gen.csr_powerlaw(4096, 4096, 0.99, seed=662)
     assert gb.auto_choice(dev(P.rowptr), P.K, dev(P.colidx), b_bytes=512 << 20, row_bytes=512)[0] == "merge"
