@@ -191,7 +191,7 @@ struct TcShape {
     static constexpr int NFA = FP8 ? NT : 2 * NT;           // 128-byte feature atoms per 8-row group
     static constexpr int BT = BPS * NFA * 1024;             // gathered B bytes per stage
     static constexpr int STAGE = BT + kATile;               // bytes per stage
-    static constexpr int S = 1;  // one stage per CTA: 5 CTAs per SM (NT <= 2) overlap better than deeper pipelines in fewer CTAs
+    static constexpr int S = 2;  // stages per CTA: the next stage is copied while this one multiplies
     static constexpr int NCOLS = NT <= 2 ? 32 : 64;         // TMEM columns (16 per feature tile)
     static constexpr int SMEM = S * STAGE + 1024 + 256;     // + alignment slack + barriers
 };

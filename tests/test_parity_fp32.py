@@ -367,3 +367,40 @@ def test_paired_default_layout_matches_strided_bitwise(gb, dt):
         paired = gb.spmm(rp, ci, v, Bd, variant=variant, ctas_per_sm=cps).cpu().numpy()
         strided = gb.spmm(rp, ci, v, Bd, variant=variant, ctas_per_sm=cps, vecs=2).cpu().numpy()
         assert np.array_equal(paired, strided)
+
+
+@pytest.mark.parametrize("Kd", [32, 64, 128])
+def test_sddmm_16_byte_aligned_operands_take_the_one_vector_layout(gb, Kd):
+    """X and Y rows 16-byte but not 32-byte aligned cannot take the paired 32-byte loads;
+    the one-vector layout must give the oracle's result just the same."""
+    import torch
+
+    A = gen.csr_powerlaw(2000, 1500, 0.99, seed=791)
+    X, Y = gen.dense_normal(A.M, Kd, 792), gen.dense_normal(A.K, Kd, 793)
+    Xb = torch.zeros(A.M * Kd + 4, device="cuda")
+    Yb = torch.zeros(A.K * Kd + 4, device="cuda")
+    Xd = Xb[4:].view(A.M, Kd)  # 16 bytes past a 256-byte boundary
+    Yd = Yb[4:].view(A.K, Kd)
+    Xd.copy_(dev(X))
+    Yd.copy_(dev(Y))
+    assert Xd.data_ptr() % 32 == 16 and Yd.data_ptr() % 32 == 16
+    out = gb.sddmm(dev(A.rowptr), dev(A.colidx), dev(A.vals), Xd, Yd).cpu().numpy()
+    ref, sc = oracle.sddmm(A.rowptr, A.colidx, A.vals, X, Y)
+    assert_within(out, ref, sc, TOL, f"sddmm one-vector layout Kd={Kd}")
+
+
+@pytest.mark.parametrize("variant", ["rowsplit", "merge"])
+def test_spmm_128_byte_rows_16_byte_aligned_b(gb, variant):
+    """FP32 N = 32 with B 16-byte but not 32-byte aligned: the strided layout instead of
+    the paired one, same result as the oracle."""
+    import torch
+
+    A = gen.csr_powerlaw(2000, 1500, 0.99, seed=794)
+    B = gen.dense_normal(A.K, 32, 795)
+    Bb = torch.zeros(A.K * 32 + 4, device="cuda")
+    Bd = Bb[4:].view(A.K, 32)
+    Bd.copy_(dev(B))
+    assert Bd.data_ptr() % 32 == 16
+    C = gb.spmm(dev(A.rowptr), dev(A.colidx), dev(A.vals), Bd, variant=variant).cpu().numpy()
+    ref, sc = oracle.spmm(A.rowptr, A.colidx, A.vals, B)
+    assert_within(C, ref, sc, TOL, f"spmm strided 128-byte rows {variant}")
