@@ -212,3 +212,48 @@ def test_sddmm_lowp_integers_bit_exact(gb):
                        x_scale=dev(np.ones(S.M, np.float32)), y_scale=dev(np.ones(S.K, np.float32)),
                        variant=variant).cpu().numpy()
         assert np.array_equal(out.astype(np.float64), want)
+
+
+# ---- every E4M3 code: the gathered operand's decode ------------------------------------------
+
+def _finite_codes():
+    """The 254 finite E4M3 codes (0x7F and 0xFF are NaN), then +0 and -0 again: 256 columns."""
+    c = np.array([q for q in range(256) if q & 0x7F != 0x7F] + [0x00, 0x80], dtype=np.uint8)
+    assert c.size == 256
+    return c
+
+
+@pytest.mark.parametrize("variant", ["rowsplit", "merge", "rowgroup", "scalar"])
+@pytest.mark.parametrize("t", [1.0, 2.0**-40, 2.0**50])
+def test_spmm_e4m3_every_code_exact(gb, variant, t):
+    """C = A B with one entry of value 1 per row (C's rows are B's rows): every finite code,
+    subnormals included, decodes to exactly the oracle's value times the row scale t."""
+    codes = _finite_codes()
+    K = 256
+    B = np.stack([np.roll(codes, k) for k in range(K)])            # every code in every column
+    rowptr = np.arange(K + 1, dtype=np.int32)
+    colidx = np.arange(K, dtype=np.int32)
+    one = oracle.e4m3_round(np.ones(K, np.float32))
+    C = gb.spmm(dev(rowptr), dev(colidx), dev(one), dev(B), a_scale=dev(np.ones(K, np.float32)),
+                b_scale=dev(np.full(K, t, np.float32)), variant=variant).cpu().numpy()
+    want = oracle.e4m3_decode(B) * t
+    assert np.array_equal(C.astype(np.float64), want)
+
+
+@pytest.mark.parametrize("variant", ["rowsplit", "merge", "entry", "scalar"])
+def test_sddmm_e4m3_every_code_exact(gb, variant):
+    """out_ij = s_ij <X_i, Y_j> with X_i the unit vector e_i: every finite code of Y read exactly."""
+    codes = _finite_codes()
+    M, Nr, Kd = 256, 64, 256
+    X = np.zeros((M, Kd), np.float32)
+    X[np.arange(M), np.arange(M)] = 1.0
+    Y = np.stack([np.roll(codes, 4 * j) for j in range(Nr)])
+    rowptr = (np.arange(M + 1) * Nr).astype(np.int32)
+    colidx = np.tile(np.arange(Nr, dtype=np.int32), M)
+    svals = np.where(np.arange(M * Nr) % 3 == 0, -0.5, 2.0).astype(np.float32)
+    out = gb.sddmm(dev(rowptr), dev(colidx), dev(svals), dev(oracle.e4m3_round(X)), dev(Y),
+                   x_scale=dev(np.ones(M, np.float32)), y_scale=dev(np.ones(Nr, np.float32)),
+                   variant=variant).cpu().numpy()
+    rows = np.repeat(np.arange(M), Nr)
+    want = svals.astype(np.float64) * oracle.e4m3_decode(Y)[colidx, rows]
+    assert np.array_equal(out.astype(np.float64), want)
