@@ -104,6 +104,25 @@ def test_gnn_chain_integers_bit_exact(gb):
         check_graph(A, sv, Hd, d[5].cpu().numpy(), d[4].float().cpu().numpy(), exact=True)
 
 
+@pytest.mark.parametrize("N", [64, 128, 256])
+def test_gnn_chain_row_lengths_bit_exact(gb, N):
+    """Empty rows and rows of 1 to 5, 31 to 33 and 70 edges in every position of a tile: the
+    short rows (at most as many edges as a group step takes) go G to a warp pass, the others
+    one after another, and both give the oracle's integers exactly."""
+    rng = np.random.default_rng(508)
+    lengths = rng.choice(np.array([0, 1, 1, 1, 2, 2, 3, 4, 5, 31, 32, 33, 70]), size=700)
+    A = gen.csr_from_lengths(lengths, 700, seed=509)
+    host, devs = build_batch([(A, N)], 510, integer=True)
+    for ept in (0, 40):
+        plan = gb.GnnPlan(devs, edges_per_tile=ept) if ept else gb.GnnPlan(devs)
+        plan.execute()
+        import torch
+
+        torch.cuda.synchronize()
+        (A, sv, Hd), d = host[0], devs[0]
+        check_graph(A, sv, Hd, d[5].cpu().numpy(), d[4].float().cpu().numpy(), exact=True)
+
+
 @pytest.mark.parametrize("edges_per_tile", [1, 64, 100000])
 def test_gnn_replay_and_tiles(gb, edges_per_tile):
     """Replays of the recorded graph follow new data in the same buffers; any tile size."""
