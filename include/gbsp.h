@@ -131,8 +131,9 @@ int sddmm_csr(const int32_t *rowptr, const int32_t *colidx, const float *svals, 
  * rowptr.  The first AUTO call on a pattern measures it and waits for the result (a
  * synchronisation); the choice is kept per (device, rowptr, colidx, rows, cols) for the
  * process (64 patterns, oldest dropped first).  Each later call uses the kept choice and
- * queues one more pass (a small kernel and a copy to pinned memory on the stream, no
- * wait); the next call adopts its result once it has arrived, so another pattern placed at
+ * queues one more pass (one small kernel on the stream that writes its counters straight
+ * into mapped pinned memory, no wait; at most one in flight per pattern); a later call
+ * adopts its result once it has arrived, so another pattern placed at
  * the same addresses gets its own choice from its second call on.  A stale choice costs
  * speed, never correctness.  Under stream capture nothing is queued: a kept choice is used,
  * else the row split.  gbsp_auto_choice reports the choice; gbsp_auto_forget drops them. */

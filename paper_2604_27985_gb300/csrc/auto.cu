@@ -21,15 +21,26 @@
 namespace gbsp {
 namespace {
 
+// What a measurement delivers, into a pinned host slot mapped into the device's address
+// space (so no copy follows the kernel).
 struct StatsOut {
     unsigned long long sumsq, empty;
     unsigned int maxlen;
+    int32_t nnz;
+};
+// A pattern's device accumulators: zero between measurements (the kernel's last block
+// resets them after delivering).
+struct StatsAcc {
+    unsigned long long sumsq, empty;
+    unsigned int maxlen, blocks_done;
 };
 
 // Grid-stride pass over the rows: per block, sum of squared lengths, empty rows and the
-// longest row (integers, so the counters and the decision do not depend on the order).
+// longest row (integers, so the counters and the decision do not depend on the order),
+// added into acc; the last block to finish writes the totals and rowptr[M] to out and
+// clears acc for the next measurement.
 __global__ void __launch_bounds__(256) row_stats_kernel(const int32_t *__restrict__ rowptr, int64_t M,
-                                                        StatsOut *out) {
+                                                        StatsAcc *acc, StatsOut *out) {
     unsigned long long sq = 0, empty = 0;
     unsigned int mx = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
@@ -59,9 +70,22 @@ __global__ void __launch_bounds__(256) row_stats_kernel(const int32_t *__restric
             empty += s_empty[w];
             mx = max(mx, s_mx[w]);
         }
-        atomicAdd(&out->sumsq, sq);
-        atomicAdd(&out->empty, empty);
-        atomicMax(&out->maxlen, mx);
+        atomicAdd(&acc->sumsq, sq);
+        atomicAdd(&acc->empty, empty);
+        atomicMax(&acc->maxlen, mx);
+        __threadfence();
+        if (atomicAdd(&acc->blocks_done, 1u) == gridDim.x - 1) {  // every block's counters are in
+            __threadfence();
+            out->sumsq = atomicAdd(&acc->sumsq, 0ull);
+            out->empty = atomicAdd(&acc->empty, 0ull);
+            out->maxlen = atomicMax(&acc->maxlen, 0u);
+            out->nnz = rowptr[M];
+            __threadfence_system();  // the host reads out once the stream's event completes
+            acc->sumsq = 0;
+            acc->empty = 0;
+            acc->maxlen = 0;
+            acc->blocks_done = 0;
+        }
     }
 }
 
@@ -71,49 +95,38 @@ struct Entry {
     int64_t rows, cols;
     int64_t stats[5];
     bool pending;      // a re-measurement is in flight (its event not yet seen complete)
-    cudaEvent_t ev;    // completion of the last measurement's copy into the host slot
-    StatsOut *h_stats;  // pinned host slot of this entry's counters
-    int32_t *h_nnz;
+    cudaEvent_t ev;    // completion of the last measurement (its counters are in the host slot)
+    StatsOut *h_stats;  // pinned host slot of this entry's counters, mapped for the device
+    StatsOut *d_stats;  // the same slot's device address
+    StatsAcc *acc;      // the pattern's device accumulators
 };
 constexpr int kCache = 64;
 std::mutex g_mu;
 Entry g_cache[kCache];
 int g_used = 0, g_next = 0;
-unsigned char *g_pinned = nullptr;  // kCache slots of 32 bytes: counters, then nnz
+unsigned char *g_pinned = nullptr;  // kCache slots of 32 bytes (StatsOut), mapped into every device
 
 bool same_key(const Entry &c, int dev, const gbsp_csr &A) {
     return c.device == dev && c.rowptr == A.rowptr && c.colidx == A.colidx && c.rows == A.rows && c.cols == A.cols;
 }
 
-// Enqueues one measurement of A's row lengths on s: the counters go to a stream-ordered
-// scratch buffer, then to the entry's pinned slot, and the entry's event marks their arrival.
+// Enqueues one measurement of A's row lengths on s: one kernel, whose counters land in the
+// entry's pinned slot; the entry's event marks their arrival.
 int enqueue_measure(const gbsp_csr &A, cudaStream_t s, Entry &e) {
-    void *d = nullptr;
-    int st = scratch_alloc(&d, sizeof(StatsOut), s);
-    if (st) return st;
-    StatsOut *dout = static_cast<StatsOut *>(d);
     int64_t blocks = (A.rows + 255) / 256;
     if (blocks > 4LL * sm_count()) blocks = 4LL * sm_count();
     if (blocks < 1) blocks = 1;
-    if (cudaMemsetAsync(dout, 0, sizeof(StatsOut), s) != cudaSuccess) st = check_launch("auto: clear");
-    if (!st) {
-        row_stats_kernel<<<(unsigned)blocks, 256, 0, s>>>(A.rowptr, A.rows, dout);
-        count_launches(1);
-        st = check_launch("auto: row statistics");
-    }
-    if (!st && (cudaMemcpyAsync(e.h_stats, dout, sizeof(StatsOut), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                cudaMemcpyAsync(e.h_nnz, A.rowptr + A.rows, sizeof(int32_t), cudaMemcpyDeviceToHost, s) !=
-                    cudaSuccess ||
-                cudaEventRecord(e.ev, s) != cudaSuccess))
-        st = check_launch("auto: read back");
-    scratch_free(d, s);
+    row_stats_kernel<<<(unsigned)blocks, 256, 0, s>>>(A.rowptr, A.rows, e.acc, e.d_stats);
+    count_launches(1);
+    int st = check_launch("auto: row statistics");
+    if (!st && cudaEventRecord(e.ev, s) != cudaSuccess) st = check_launch("auto: event");
     return st;
 }
 
 // Reads the entry's pinned slot into its statistics and decision.
 void adopt(Entry &e) {
     e.stats[0] = e.rows;
-    e.stats[1] = *e.h_nnz;
+    e.stats[1] = e.h_stats->nnz;
     e.stats[2] = (int64_t)e.h_stats->sumsq;
     e.stats[3] = (int64_t)e.h_stats->maxlen;
     e.stats[4] = (int64_t)e.h_stats->empty;
@@ -209,7 +222,8 @@ int auto_choice(const gbsp_csr &A, int op, int64_t b_bytes, int64_t row_bytes, c
     }
     // a new pattern: take a slot (the oldest when all are used) and measure now
     if (!g_pinned) {
-        if (cudaHostAlloc(&g_pinned, (size_t)kCache * 32, cudaHostAllocPortable) != cudaSuccess) {
+        if (cudaHostAlloc(&g_pinned, (size_t)kCache * 32, cudaHostAllocPortable | cudaHostAllocMapped) !=
+            cudaSuccess) {
             g_pinned = nullptr;
             cudaGetLastError();
             return fail(GBSP_ERR_OOM, "auto: pinned host slots could not be allocated");
@@ -218,8 +232,9 @@ int auto_choice(const gbsp_csr &A, int op, int64_t b_bytes, int64_t row_bytes, c
     const int slot = g_next;
     Entry &e = g_cache[slot];
     if (slot < g_used && e.ev) {
-        if (e.pending) cudaEventSynchronize(e.ev);  // its copy targets the slot being reused
+        if (e.pending) cudaEventSynchronize(e.ev);  // its kernel writes the slot being reused
         cudaEventDestroy(e.ev);
+        cudaFree(e.acc);
     }
     e = Entry{};
     if (cudaEventCreateWithFlags(&e.ev, cudaEventDisableTiming) != cudaSuccess) {
@@ -232,9 +247,20 @@ int auto_choice(const gbsp_csr &A, int op, int64_t b_bytes, int64_t row_bytes, c
     e.rows = A.rows;
     e.cols = A.cols;
     e.h_stats = reinterpret_cast<StatsOut *>(g_pinned + 32 * slot);
-    e.h_nnz = reinterpret_cast<int32_t *>(g_pinned + 32 * slot + 24);
+    void *dslot = nullptr;
+    if (cudaHostGetDevicePointer(&dslot, e.h_stats, 0) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void **>(&e.acc), sizeof(StatsAcc)) != cudaSuccess ||
+        cudaMemsetAsync(e.acc, 0, sizeof(StatsAcc), s) != cudaSuccess) {
+        st = check_launch("auto: counters");
+        cudaFree(e.acc);
+        cudaEventDestroy(e.ev);
+        e = Entry{};
+        return st ? st : fail(GBSP_ERR_CUDA, "auto: counters");
+    }
+    e.d_stats = static_cast<StatsOut *>(dslot);
     if ((st = enqueue_measure(A, s, e)) || cudaEventSynchronize(e.ev) != cudaSuccess) {
         if (!st) st = check_launch("auto: measurement");
+        cudaFree(e.acc);
         cudaEventDestroy(e.ev);
         e = Entry{};
         return st;
@@ -255,6 +281,7 @@ void auto_forget_all() {
             if (g_cache[k].pending) cudaEventSynchronize(g_cache[k].ev);
             cudaEventDestroy(g_cache[k].ev);
         }
+        cudaFree(g_cache[k].acc);
         g_cache[k] = Entry{};
     }
     g_used = 0;
